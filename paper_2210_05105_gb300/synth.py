@@ -1,0 +1,108 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module only draws data: COO coordinates, values and the N(0,1) initial
+factors.  It holds none of the CP-ALS arithmetic, so the oracle and the CUDA
+library can both be fed from it without sharing any of the method's code.
+
+Recipe (stand-ins for the FROSTT tensors of the paper's Table 5, which are not
+redistributed here):
+* Each mode index is pi_n(rank), rank drawn from a truncated Zipf law
+  P(rank = r) proportional to (r + 1)^-s for r < I_n by inverse CDF over a
+  binary64 table; pi_n is a seeded random permutation (the random index
+  permutation of the paper's Sec. 4.4 load-balancing).  s = 0 gives uniform
+  coordinates.
+* Coordinates are made distinct by their linear key; draws continue until
+  exactly nnz distinct coordinates exist, keeping the earliest-drawn ones.
+* Values: uniform(0, 1), lognormal(0, 1), or log(1 + Poisson(3)) with zero
+  draws redrawn (Reddit-like log counts).
+All randomness comes from numpy's PCG64 with the caller's seed.
+"""
+import numpy as np
+
+
+def _zipf_table(I, s):
+    r = np.arange(1, I + 1, dtype=np.float64)
+    w = r ** (-float(s)) if s else np.ones(I)
+    c = np.cumsum(w)
+    return c / c[-1]
+
+
+def _draw_indices(rng, dims, count, s, perms, tables):
+    out = np.empty((len(dims), count), dtype=np.int64)
+    for k, I in enumerate(dims):
+        if s == 0:
+            out[k] = rng.integers(0, I, size=count)
+        else:
+            u = rng.random(count)
+            rank = np.minimum(np.searchsorted(tables[k], u, side="right"), I - 1)
+            out[k] = perms[k][rank]
+    return out
+
+
+def coo_coordinates(dims, nnz, seed, zipf_s=0.0):
+    """Exactly nnz distinct coordinates, (N, nnz) int32, earliest draws kept."""
+    dims = [int(d) for d in dims]
+    total = 1
+    for d in dims:
+        total *= d
+    if nnz > total:
+        raise ValueError("nnz exceeds the number of cells")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perms = [rng.permutation(I) for I in dims] if zipf_s else None
+    tables = [_zipf_table(I, zipf_s) for I in dims] if zipf_s else None
+    mult = np.ones(len(dims), dtype=np.uint64)
+    for k in range(1, len(dims)):
+        mult[k] = mult[k - 1] * np.uint64(dims[k - 1])
+    drawn = np.empty((len(dims), 0), dtype=np.int64)
+    need = nnz
+    while True:
+        batch = max(1024, int(need * 1.15) + 16)
+        drawn = np.concatenate([drawn, _draw_indices(rng, dims, batch, zipf_s, perms, tables)], axis=1)
+        keys = np.zeros(drawn.shape[1], dtype=np.uint64)
+        for k in range(len(dims)):
+            keys += drawn[k].astype(np.uint64) * mult[k]
+        _, first = np.unique(keys, return_index=True)
+        if first.size >= nnz:
+            keep = np.sort(first)[:nnz]
+            return drawn[:, keep].astype(np.int32)
+        need = nnz - first.size
+        drawn = drawn[:, np.sort(first)]
+
+
+def coo_values(nnz, seed, kind="uniform"):
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    if kind == "uniform":
+        return rng.random(nnz, dtype=np.float32)
+    if kind == "lognormal":
+        return rng.lognormal(0.0, 1.0, size=nnz).astype(np.float32)
+    if kind == "logpoisson":
+        x = rng.poisson(3.0, size=nnz)
+        bad = x == 0
+        while bad.any():
+            x[bad] = rng.poisson(3.0, size=int(bad.sum()))
+            bad = x == 0
+        return np.log1p(x.astype(np.float64)).astype(np.float32)
+    raise ValueError(kind)
+
+
+def init_factors(dims, R, seed):
+    """Unit-variance Gaussian initial factors (I_k, R) float32 (Algorithm 1 line 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [rng.standard_normal((int(I), R), dtype=np.float32) for I in dims]
+
+
+def make_tensor(dims, nnz, seed, zipf_s=0.0, values="uniform"):
+    idx = coo_coordinates(dims, nnz, seed, zipf_s)
+    vals = coo_values(nnz, seed, values)
+    return idx, vals
+
+
+# Named workloads (dims, nnz, Zipf exponent, value law, R, J, sweeps, seeds)
+WORKLOADS = {
+    "small_uniform_200x150x100": dict(dims=(200, 150, 100), nnz=20_000, zipf=0.0,
+                                      values="uniform", R=8, J=2000, sweeps=5,
+                                      data_seed=1001, init_seed=2001, sample_seed=3001),
+    "zipf_1e5cube_50M": dict(dims=(100_000, 100_000, 100_000), nnz=50_000_000, zipf=1.1,
+                             values="lognormal", R=32, J=65536, sweeps=20,
+                             data_seed=1002, init_seed=2002, sample_seed=3002),
+}
