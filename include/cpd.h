@@ -1,0 +1,195 @@
+/*
+ * cpd.h -- C ABI of libcpd: randomized sparse CP decomposition on one GB300.
+ *
+ * Method: V. Bharadwaj, O. A. Malik, R. Murray, A. Buluc, J. Demmel,
+ * "Distributed-Memory Randomized Algorithms for Sparse Tensor CP
+ * Decomposition" (arXiv 2210.05105).  Per mode n of each ALS round
+ * (Algorithm 1) the library
+ *   1. draws J rows of the Khatri-Rao product U_{!=n} (Eq. 3) by leverage
+ *      scores: CP-ARLS-LEV (product of per-factor leverage scores, Appendix A,
+ *      Algorithms 2-3) or STS-CP (exact leverage by a random walk on a binary
+ *      tree of block Grams, Sec. 4.1 and Appendix B, Algorithms 4-5);
+ *   2. computes the downsampled MTTKRP  Y = mat(T, n) S^T S U_{!=n}  (Eq. 7);
+ *   3. solves  U_n = Y G^+  with G = *_{k != n} U_k^T U_k  (Eq. 4, Eq. 5) and
+ *      renormalises the columns of U_n into sigma (Algorithm 1 lines 6-8).
+ *
+ * Conventions shared by every entry point
+ *   - Modes are 0-based; 1 <= N <= CPD_MAX_MODES.  Ranks 1 <= R <= CPD_MAX_RANK.
+ *   - Factor U_k is I_k x R, row-major float32 with row stride R (the library
+ *     keeps its own padded copy).
+ *   - A "KRP row" of U_{!=n} is a tuple (i_k)_{k != n}; its linear key is
+ *     sum_{k != n} i_k * prod_{k' < k, k' != n} I_k' (lowest mode fastest,
+ *     the row order of Eq. 3).
+ *   - Unless stated otherwise pointers are DEVICE pointers on the device that
+ *     was current at cpd_create; calls are asynchronous on the handle's
+ *     stream and return after enqueueing.
+ *   - Host-checkable argument errors are returned at the call.  Errors found
+ *     by kernels (index out of range, capacity overflow, a bounded wait that
+ *     gave up) are latched in a device status word and returned by the next
+ *     synchronising call (cpd_synchronize, cpd_fit, cpd_get_*).
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Memory passed in stays owned by the caller; memory inside a handle is
+ *     owned by the library and released by cpd_destroy.
+ */
+#ifndef CPD_H
+#define CPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPD_MAX_MODES 8
+#define CPD_MAX_RANK 128
+
+typedef struct cpd_ctx* cpd_handle;
+
+typedef enum {
+  CPD_OK = 0,
+  CPD_ERR_INVALID_ARG = 1,       /* bad size, null pointer, unsupported option */
+  CPD_ERR_OUT_OF_RANGE_INDEX = 2,/* a coordinate or sample index >= I_k or < 0 */
+  CPD_ERR_DUPLICATE = 3,         /* two nonzeros share one coordinate */
+  CPD_ERR_OOM = 4,               /* device allocation failed */
+  CPD_ERR_CUDA = 5,              /* a CUDA runtime call failed; see cpd_last_error */
+  CPD_ERR_CAPACITY = 6,          /* more samples / selected nonzeros than allocated */
+  CPD_ERR_SINGULAR_GRAM = 7,     /* reserved: pseudo-inverse failed to converge */
+  CPD_ERR_TIMEOUT = 8,           /* a bounded device-side wait gave up */
+  CPD_ERR_NOT_FINITE = 9         /* NaN or Inf in values or factors */
+} cpd_status;
+
+typedef enum {
+  CPD_ARLS_LEV = 0,  /* CP-ARLS-LEV: product of per-factor leverage scores */
+  CPD_STS_CP = 1,    /* STS-CP: exact leverage scores by tree random walks */
+  CPD_EXACT = 2      /* non-randomized ALS: full MTTKRP of Eq. 6 */
+} cpd_method;
+
+typedef struct {
+  int32_t method;          /* cpd_method */
+  int32_t rank;            /* R */
+  int64_t samples;         /* J, draws per mode update (capacity for caller lists) */
+  uint64_t seed;           /* Philox4x64-10 key word 0 for all draws */
+  int32_t leaf_rows;       /* STS-CP rows per tree leaf F; 0 means F = R */
+  int32_t input_on_host;   /* 1: idx, vals, init_factors of cpd_create are host memory */
+  int64_t reserved_i64[4];
+  int32_t reserved_i32[8];
+} cpd_options;
+
+/* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */
+cpd_status cpd_default_options(cpd_options* opt);
+
+/*
+ * Build a handle for the N-mode sparse tensor given as COO (Sec. 3: a list of
+ * (N+1)-tuples).
+ *   dims          host, N entries, I_k >= 1; prod of all I_k must be < 2^64.
+ *   nnz           number of nonzeros, 0 <= nnz < 2^32 - 1.
+ *   idx           N x nnz int32, mode-major (idx[k * nnz + e] = i_k of nonzero e).
+ *   vals          nnz float32.
+ *   init_factors  concatenated U_0 .. U_{N-1}, each I_k x R row-major float32
+ *                 (the N(0,1) draws of Algorithm 1 line 1); must not be NULL.
+ *   cuda_stream   cudaStream_t the handle enqueues on (NULL: legacy stream).
+ * The library copies and re-sorts the inputs (one layout per matricization,
+ * sorted by KRP-row key, with a hash index from key to its nonzeros, Sec. 4.3)
+ * and normalises the factors (Algorithm 1 lines 2-3).  Coordinates must be
+ * distinct (CPD_ERR_DUPLICATE otherwise).  Synchronises the stream.
+ */
+cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz,
+                      const int32_t* idx, const float* vals,
+                      const float* init_factors, const cpd_options* opt,
+                      void* cuda_stream, cpd_handle* out);
+
+/*
+ * Draw J rows of U_{!=mode} with the handle's method (CP-ARLS-LEV:
+ * Algorithm 3 with one processor; STS-CP: Algorithm 5 with one processor),
+ * from the handle's current factors.  Uniform u(j, k) = Philox4x64-10 with
+ * key (seed, stream) and counter (j, k, mode, sweep), top 53 bits of word 0
+ * times 2^-53; stream 0 for CP-ARLS-LEV and 1 for STS-CP.
+ *   out_idx   N x J int32 (row `mode` is written as -1).
+ *   out_prob  J float64: probability of the drawn KRP row (ARLS: product of
+ *             ell_k[i_k] / C_k; STS: exact leverage / <G^+, G>).
+ * 1 <= J <= options.samples.
+ */
+cpd_status cpd_leverage_sample(cpd_handle h, int32_t mode, int64_t J, uint64_t sweep,
+                               int32_t* out_idx, double* out_prob);
+
+/*
+ * Downsampled MTTKRP Y = mat(T, mode) S^T S U_{!=mode} (Eq. 7): draw j selects
+ * the KRP row idx[:, j] with weight w[j] on the diagonal of S^T S; repeated
+ * rows add their weights.  Y (I_mode x R float32, row-major) is overwritten.
+ *   idx  N x J int32 (row `mode` ignored);  w  J float64.
+ *   out_nnz_sel  device int64 or NULL: receives nnz(mat(T, mode) S^T), the
+ *                nonzeros in the distinct sampled columns.
+ * 0 <= J <= options.samples; indices out of range latch
+ * CPD_ERR_OUT_OF_RANGE_INDEX and the draw is skipped.
+ */
+cpd_status cpd_sampled_mttkrp(cpd_handle h, int32_t mode, const int32_t* idx,
+                              const double* w, int64_t J, float* Y,
+                              int64_t* out_nnz_sel);
+
+/*
+ * Exact MTTKRP Y = mat(T, mode) U_{!=mode} (Eq. 6) over all nonzeros.
+ * Y: I_mode x R float32, overwritten.
+ */
+cpd_status cpd_exact_mttkrp(cpd_handle h, int32_t mode, float* Y);
+
+/*
+ * Solve step of Algorithm 1 for `mode` given Y: U_mode := Y G^+ with
+ * G = *_{k != mode} U_k^T U_k (Eq. 4, 5; pseudo-inverse by Cholesky, or by a
+ * Jacobi eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped
+ * when G is singular), sigma_r := ||U_mode[:, r]||, U_mode[:, r] /= sigma_r
+ * (sigma_r = 0 leaves the column as is).  Then refreshes U_mode's Gram and
+ * sampler (Algorithm 2 or 4).
+ *   Y          I_mode x R float32 (may be the buffer given to cpd_sampled_mttkrp).
+ *   out_sigma  R float64, or NULL.
+ */
+cpd_status cpd_gram_solve(cpd_handle h, int32_t mode, const float* Y, double* out_sigma);
+
+/*
+ * n_sweeps ALS rounds (Algorithm 1 lines 4-9), each updating modes 0..N-1 in
+ * order with sample, MTTKRP and solve; sweep s of the handle (counted from 0
+ * at creation) uses counter word s.  The first call captures one round as a
+ * CUDA graph; later rounds replay it.
+ */
+cpd_status cpd_als_sweep(cpd_handle h, int32_t n_sweeps);
+
+/*
+ * fit = 1 - ||T~ - T||_F / ||T||_F (Sec. 5.1) of the current model, computed
+ * as ||T||^2 - 2 <T, T~> + sigma^T (*_k G_k) sigma in float64.  out_fit is a
+ * HOST pointer.  Synchronises.
+ */
+cpd_status cpd_fit(cpd_handle h, double* out_fit);
+
+/* Copy U_mode (I_mode x R float32 row-major) to / from dst / src, host or
+ * device (any pointer cudaMemcpy accepts).  cpd_get_factors synchronises;
+ * cpd_set_factors also refreshes the mode's Gram and sampler. */
+cpd_status cpd_get_factors(cpd_handle h, int32_t mode, float* dst);
+cpd_status cpd_set_factors(cpd_handle h, int32_t mode, const float* src);
+
+/* Copy sigma (R float64) to dst, host or device.  Synchronises. */
+cpd_status cpd_get_sigma(cpd_handle h, double* dst);
+
+/*
+ * Copy the CP-ARLS-LEV sampler state of `mode` (Algorithm 2): ell (I_mode
+ * float64 leverage scores of U_mode alone) and cdf (I_mode float64 running
+ * sums, cdf[I-1] = C); either pointer may be NULL.  Host or device.
+ * Synchronises.  CPD_ERR_INVALID_ARG if the handle's method is not ARLS.
+ */
+cpd_status cpd_get_arls_state(cpd_handle h, int32_t mode, double* ell, double* cdf);
+
+/* Copy the Gram U_mode^T U_mode (R x R float64).  Synchronises. */
+cpd_status cpd_get_gram(cpd_handle h, int32_t mode, double* dst);
+
+/* Wait for the handle's stream and return the first latched device error. */
+cpd_status cpd_synchronize(cpd_handle h);
+
+/* Text of the most recent error on this handle (static storage, never NULL). */
+const char* cpd_last_error(cpd_handle h);
+
+/* Release every allocation of the handle.  Synchronises.  NULL is a no-op. */
+void cpd_destroy(cpd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPD_H */

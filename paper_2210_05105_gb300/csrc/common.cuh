@@ -1,0 +1,190 @@
+// Shared declarations of libcpd: the handle, device helpers and launchers.
+// Written for sm_103a (GB300): 152 SMs, 32-wide warps, FP64 at 1/64 of FP32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include "../../include/cpd.h"
+
+#define CPD_WARP 32
+#define CPD_FULL 0xffffffffu
+#define CPD_EMPTY32 0xffffffffu
+#define CPD_EMPTY64 0xffffffffffffffffull
+
+// round-up helpers
+__host__ __device__ static inline int64_t cpd_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int cpd_pad4(int r) { return (r + 3) & ~3; }
+
+// Slot of the per-mode hash index: KRP-row key -> nonzero range [beg, beg+len)
+// in the mode's key-sorted nonzero array.  16 bytes, one vector load.
+struct __align__(16) FiberSlot {
+  unsigned long long key;   // CPD_EMPTY64 when free
+  uint32_t beg;
+  uint32_t len;
+};
+
+// Per-mode layout (one matricization mat(T, n), Sec. 4.3): nonzeros sorted by
+// their KRP-row key, packed (row i_n, value bits) pairs, plus the hash index.
+struct ModeLayout {
+  uint2* ent = nullptr;            // nnz: x = i_n, y = __float_as_uint(val)
+  FiberSlot* table = nullptr;      // capacity = mask + 1 (power of two)
+  unsigned long long mask = 0;
+  int64_t n_fibers = 0;
+  unsigned long long stride[CPD_MAX_MODES] = {0};  // key strides, 0 for mode n
+};
+
+// Device status codes are cpd_status values; 0 = fine.
+struct cpd_ctx {
+  int N = 0, R = 0, Rp = 0;   // Rp: row stride of factor storage (R rounded to 4)
+  int64_t dims[CPD_MAX_MODES] = {0};
+  int64_t nnz = 0, Imax = 0;
+  cpd_options opt;
+  cudaStream_t stream = nullptr;      // caller's stream (NULL: legacy default stream)
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture the sweep graph
+  int device = 0, num_sms = 0;
+  std::string last_error;
+
+  // tensor in input order (for the fit and the exact MTTKRP)
+  int32_t* idx = nullptr;   // N x nnz
+  float* vals = nullptr;
+  double tnorm2 = 0.0;      // ||T||_F^2
+  ModeLayout mode[CPD_MAX_MODES];
+
+  // model
+  float* U[CPD_MAX_MODES] = {nullptr};      // I_k x Rp, padded columns zero
+  double* G[CPD_MAX_MODES] = {nullptr};     // R x R Gram of U_k
+  double* sigma = nullptr;                  // R
+
+  // CP-ARLS-LEV state (Algorithm 2) per factor
+  double* Gkpinv[CPD_MAX_MODES] = {nullptr};  // R x R
+  double* Bk[CPD_MAX_MODES] = {nullptr};      // R x R, G_k^+ = B^T B
+  int* Btri = nullptr;                        // N flags: B lower triangular
+  double* ell[CPD_MAX_MODES] = {nullptr};     // I_k
+  double* cdf[CPD_MAX_MODES] = {nullptr};     // I_k inclusive running sums
+  double* blk[CPD_MAX_MODES] = {nullptr};     // per-block partial sums of ell
+
+  // STS-CP state (Algorithm 4) per factor: heap of 2L node Grams
+  int F = 0;
+  int64_t L[CPD_MAX_MODES] = {0};
+  double* tree64[CPD_MAX_MODES] = {nullptr};  // 2L x R x R float64
+  float* tree32[CPD_MAX_MODES] = {nullptr};   // 2L x R x R float32 copy
+
+  // per-update work buffers
+  double* Gn = nullptr;        // R x R Hadamard of Grams for the solved mode
+  double* Gnpinv = nullptr;    // R x R its pseudo-inverse
+  double* Gpart = nullptr;     // Gram partial sums: gram_blocks x R x R
+  int gram_blocks = 0;
+  double* colsq = nullptr;     // column sum-of-squares partials: gram_blocks x R
+  int32_t* samp_idx = nullptr; // N x J
+  double* samp_p = nullptr;    // J
+  double* samp_w = nullptr;    // J
+  float* Y = nullptr;          // Imax x Rp
+  float* Uwork = nullptr;      // Imax x Rp (unnormalised solve output)
+
+  // sampled-MTTKRP scratch (sized from J)
+  int64_t Jcap = 0;
+  uint32_t dedup_mask = 0;
+  uint32_t* dd_tag = nullptr;  // dedup capacity: fiber begin offset or EMPTY
+  double* dd_w = nullptr;      // summed weight per distinct sampled column
+  uint32_t* uq_slot = nullptr; // Jcap: dedup slot of each distinct column
+  uint32_t* uq_len = nullptr;  // Jcap
+  uint32_t* uq_off = nullptr;  // Jcap + 1 exclusive offsets into the flat list
+  float* H = nullptr;          // Jcap x Rp: KRP row of each distinct column
+  uint32_t* counters = nullptr;// [0] distinct columns, [1] nnz_sel (low), [2..] spare
+  int* status = nullptr;       // latched device error (cpd_status)
+  double* fit_out = nullptr;   // 2 doubles: <T, T~>, ||T~||^2
+  unsigned long long* sweep_ctr = nullptr;  // device sweep counter for graphs
+
+  // graph of one ALS round
+  cudaGraphExec_t sweep_exec = nullptr;
+  cudaGraph_t sweep_graph = nullptr;
+  unsigned long long host_sweep = 0;
+
+  std::vector<void*> allocs;
+};
+
+// ---- error helpers -------------------------------------------------------
+cpd_status cpd_fail(cpd_ctx* h, cpd_status s, const std::string& msg);
+cpd_status cpd_cuda_check(cpd_ctx* h, cudaError_t e, const char* what);
+#define CPD_CUDA(h, call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return cpd_cuda_check((h), _e, #call); } while (0)
+#define CPD_LAUNCH(h, what) do { cudaError_t _e = cudaGetLastError(); if (_e != cudaSuccess) return cpd_cuda_check((h), _e, what); } while (0)
+template <typename T> cpd_status cpd_alloc(cpd_ctx* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) { cudaGetLastError(); return cpd_fail(h, CPD_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)); }
+  h->allocs.push_back((void*)*p);
+  return CPD_OK;
+}
+
+// ---- device helpers ------------------------------------------------------
+__device__ __forceinline__ void cpd_set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CPD_FULL, v, o);
+  return v;
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood, "Fast splittable pseudorandom
+// number generators", OOPSLA'14): hash of a KRP-row key to a table slot.
+__device__ __forceinline__ unsigned long long cpd_mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): one block of 4 words.
+__device__ __forceinline__ void cpd_philox4x64(unsigned long long c[4], unsigned long long k0,
+                                               unsigned long long k1) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += W0; k1 += W1; }
+    unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    unsigned long long x0 = hi1 ^ c[1] ^ k0, x2 = hi0 ^ c[3] ^ k1;
+    c[0] = x0; c[1] = lo1; c[2] = x2; c[3] = lo0;
+  }
+}
+
+// u(seed, stream; j, k, n, s) in [0, 1): top 53 bits of word 0 times 2^-53.
+__device__ __forceinline__ double cpd_uniform(unsigned long long seed, unsigned long long stream,
+                                              unsigned long long j, unsigned long long k,
+                                              unsigned long long n, unsigned long long s) {
+  unsigned long long c[4] = {j, k, n, s};
+  cpd_philox4x64(c, seed, stream);
+  return (double)(c[0] >> 11) * 0x1.0p-53;
+}
+
+#define CPD_STREAM_ARLS 0ull
+#define CPD_STREAM_STS 1ull
+
+// ---- launchers implemented across the .cu files --------------------------
+// layout.cu
+cpd_status cpd_build_layouts(cpd_ctx* h);
+// dense.cu
+cpd_status cpd_renormalize_inputs(cpd_ctx* h);
+cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G);
+cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout);
+cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P, double* B, int* tri);
+cpd_status cpd_dense_init(cpd_ctx* h);
+cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_sigma);
+cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out);
+// sample.cu
+cpd_status cpd_refresh_sampler(cpd_ctx* h, int mode);
+cpd_status cpd_sample_init(cpd_ctx* h);
+cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep,
+                    unsigned long long sweep, int32_t* out_idx, double* out_p, double* out_w);
+// mttkrp.cu
+cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, const double* w,
+                                     const double* p, int64_t J, float* Y, int64_t* out_nnz_sel);
+cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y);
+// scan.cu
+cpd_status cpd_scan_u32(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);
+cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t n, int bits,
+                              unsigned long long* keys_tmp, uint32_t* vals_tmp);

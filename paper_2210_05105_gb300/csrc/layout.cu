@@ -1,0 +1,210 @@
+// Per-mode layouts of the sparse tensor (Sec. 4.3, "Tensor Storage and Local
+// MTTKRP"): for each matricization mat(T, n) the nonzeros are sorted by the
+// key of their column (the KRP row of U_{!=n} they pair with), so that the
+// nonzeros of one sampled column form one contiguous range.  A hash index maps
+// a column key to that range, which replaces the paper's sorted-column search.
+#include "common.cuh"
+#include <algorithm>
+
+namespace {
+
+__global__ void check_indices_kernel(const int32_t* __restrict__ idx, int64_t nnz, int N,
+                                     const int64_t* __restrict__ dims, const float* __restrict__ vals,
+                                     int* status) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; e < nnz; e += st) {
+    for (int k = 0; k < N; ++k) {
+      int32_t i = idx[(int64_t)k * nnz + e];
+      if (i < 0 || (int64_t)i >= dims[k]) cpd_set_status(status, CPD_ERR_OUT_OF_RANGE_INDEX);
+    }
+    if (!isfinite(vals[e])) cpd_set_status(status, CPD_ERR_NOT_FINITE);
+  }
+}
+
+// key of nonzero e for mode n; for the first layout (n == 0) the row index is
+// appended below the key (full linear index), which lets one sort both group
+// the columns and expose duplicate coordinates as equal neighbours.
+struct KeyArgs {
+  unsigned long long stride[CPD_MAX_MODES];
+  int N, n;
+  unsigned long long In;
+  int full;
+};
+
+__global__ void make_keys_kernel(const int32_t* __restrict__ idx, int64_t nnz, KeyArgs a,
+                                 unsigned long long* __restrict__ keys, uint32_t* __restrict__ perm) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; e < nnz; e += st) {
+    unsigned long long key = 0;
+    for (int k = 0; k < a.N; ++k)
+      if (k != a.n) key += (unsigned long long)idx[(int64_t)k * nnz + e] * a.stride[k];
+    if (a.full) key = key * a.In + (unsigned long long)idx[(int64_t)a.n * nnz + e];
+    keys[e] = key;
+    perm[e] = (uint32_t)e;
+  }
+}
+
+// After sorting by full linear index, equal neighbours are duplicate coordinates.
+__global__ void duplicate_check_kernel(const unsigned long long* __restrict__ keys, int64_t nnz, int* status) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; e < nnz; e += st)
+    if (e > 0 && keys[e] == keys[e - 1]) cpd_set_status(status, CPD_ERR_DUPLICATE);
+}
+
+__global__ void divide_keys_kernel(unsigned long long* __restrict__ keys, int64_t nnz, unsigned long long In) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; e < nnz; e += st) keys[e] = keys[e] / In;
+}
+
+__global__ void gather_entries_kernel(const int32_t* __restrict__ idx_n, const float* __restrict__ vals,
+                                      const uint32_t* __restrict__ perm, int64_t nnz, uint2* __restrict__ ent,
+                                      const unsigned long long* __restrict__ keys, uint32_t* __restrict__ flags) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; e < nnz; e += st) {
+    uint32_t p = perm[e];
+    ent[e] = make_uint2((uint32_t)idx_n[p], __float_as_uint(vals[p]));
+    flags[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1u : 0u;
+  }
+}
+
+__global__ void fiber_begin_kernel(const uint32_t* __restrict__ flags_in, const uint32_t* __restrict__ fid,
+                                   int64_t nnz, uint32_t* __restrict__ fbeg) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; e < nnz; e += st)
+    if (flags_in[e]) fbeg[fid[e]] = (uint32_t)e;
+}
+
+__global__ void table_insert_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ fbeg,
+                                    int64_t nf, uint32_t nnz, FiberSlot* __restrict__ table,
+                                    unsigned long long mask, int* status) {
+  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; f < nf; f += st) {
+    uint32_t b = fbeg[f];
+    uint32_t e = (f + 1 < nf) ? fbeg[f + 1] : nnz;
+    unsigned long long key = keys[b];
+    unsigned long long s = cpd_mix64(key) & mask;
+    bool placed = false;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+      unsigned long long old = atomicCAS(&table[s].key, CPD_EMPTY64, key);
+      if (old == CPD_EMPTY64) {
+        table[s].beg = b;
+        table[s].len = e - b;
+        placed = true;
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+    if (!placed) cpd_set_status(status, CPD_ERR_CAPACITY);
+  }
+}
+
+int bits_for(unsigned long long maxval) {
+  int b = 0;
+  while (b < 64 && (maxval >> b) != 0ull) ++b;
+  return b;
+}
+
+}  // namespace
+
+cpd_status cpd_build_layouts(cpd_ctx* h) {
+  const int64_t nnz = h->nnz;
+  const int N = h->N;
+  cudaStream_t st = h->stream;
+  const int grid = h->num_sms * 8, thr = 256;
+
+  int64_t* d_dims = nullptr;
+  CPD_CUDA(h, cudaMallocAsync((void**)&d_dims, sizeof(int64_t) * CPD_MAX_MODES, st));
+  CPD_CUDA(h, cudaMemcpyAsync(d_dims, h->dims, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
+  if (nnz > 0) {
+    check_indices_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, N, d_dims, h->vals, h->status);
+    CPD_LAUNCH(h, "check_indices");
+  }
+  int hs = 0;
+  CPD_CUDA(h, cudaMemcpyAsync(&hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPD_CUDA(h, cudaStreamSynchronize(st));
+  CPD_CUDA(h, cudaFreeAsync(d_dims, st));
+  if (hs != 0) {
+    return cpd_fail(h, (cpd_status)hs, hs == CPD_ERR_OUT_OF_RANGE_INDEX ? "coordinate out of range"
+                                                                      : "non-finite tensor value");
+  }
+
+  unsigned long long *keys = nullptr, *keys_tmp = nullptr;
+  uint32_t *perm = nullptr, *perm_tmp = nullptr, *flags = nullptr, *fid = nullptr;
+  size_t m = (size_t)std::max<int64_t>(nnz, 1);
+  CPD_CUDA(h, cudaMallocAsync((void**)&keys, m * 8, st));
+  CPD_CUDA(h, cudaMallocAsync((void**)&keys_tmp, m * 8, st));
+  CPD_CUDA(h, cudaMallocAsync((void**)&perm, m * 4, st));
+  CPD_CUDA(h, cudaMallocAsync((void**)&perm_tmp, m * 4, st));
+  CPD_CUDA(h, cudaMallocAsync((void**)&flags, m * 4, st));
+  CPD_CUDA(h, cudaMallocAsync((void**)&fid, m * 4, st));
+
+  for (int n = 0; n < N; ++n) {
+    ModeLayout& L = h->mode[n];
+    KeyArgs a;
+    unsigned long long acc = 1;
+    for (int k = 0; k < CPD_MAX_MODES; ++k) a.stride[k] = 0;
+    for (int k = 0; k < N; ++k) {
+      if (k == n) continue;
+      a.stride[k] = acc;
+      L.stride[k] = acc;
+      acc *= (unsigned long long)h->dims[k];
+    }
+    a.N = N; a.n = n; a.In = (unsigned long long)h->dims[n]; a.full = (n == 0);
+    unsigned long long maxkey = acc - 1ull;            // largest column key
+    if (n == 0) maxkey = acc * a.In - 1ull;            // full linear index
+    cpd_status s = cpd_alloc(h, &L.ent, m);
+    if (s != CPD_OK) return s;
+    if (nnz == 0) {
+      L.n_fibers = 0;
+      L.mask = 15;
+      if ((s = cpd_alloc(h, &L.table, 16)) != CPD_OK) return s;
+      CPD_CUDA(h, cudaMemsetAsync(L.table, 0xff, 16 * sizeof(FiberSlot), st));
+      continue;
+    }
+    make_keys_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, a, keys, perm);
+    CPD_LAUNCH(h, "make_keys");
+    if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(maxkey), keys_tmp, perm_tmp)) != CPD_OK) return s;
+    if (n == 0) {
+      duplicate_check_kernel<<<grid, thr, 0, st>>>(keys, nnz, h->status);
+      divide_keys_kernel<<<grid, thr, 0, st>>>(keys, nnz, a.In);
+      CPD_LAUNCH(h, "duplicate check");
+    }
+    gather_entries_kernel<<<grid, thr, 0, st>>>(h->idx + (int64_t)n * nnz, h->vals, perm, nnz, L.ent, keys, flags);
+    CPD_LAUNCH(h, "gather_entries");
+    uint32_t* d_total = (uint32_t*)keys_tmp;   // scratch word
+    if ((s = cpd_scan_u32(h, flags, fid, nnz, d_total)) != CPD_OK) return s;
+    uint32_t nf = 0;
+    CPD_CUDA(h, cudaMemcpyAsync(&nf, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CPD_CUDA(h, cudaMemcpyAsync(&hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPD_CUDA(h, cudaStreamSynchronize(st));
+    if (hs == CPD_ERR_DUPLICATE) return cpd_fail(h, CPD_ERR_DUPLICATE, "duplicate coordinates in the COO input");
+    L.n_fibers = nf;
+    uint32_t* fbeg = perm_tmp;   // reuse: the sort is done
+    fiber_begin_kernel<<<grid, thr, 0, st>>>(flags, fid, nnz, fbeg);
+    CPD_LAUNCH(h, "fiber_begin");
+    unsigned long long cap = 16;
+    while (cap < 2ull * (unsigned long long)nf) cap <<= 1;
+    L.mask = cap - 1;
+    if ((s = cpd_alloc(h, &L.table, cap)) != CPD_OK) return s;
+    CPD_CUDA(h, cudaMemsetAsync(L.table, 0xff, cap * sizeof(FiberSlot), st));
+    table_insert_kernel<<<grid, thr, 0, st>>>(keys, fbeg, nf, (uint32_t)nnz, L.table, L.mask, h->status);
+    CPD_LAUNCH(h, "table_insert");
+  }
+  CPD_CUDA(h, cudaFreeAsync(keys, st));
+  CPD_CUDA(h, cudaFreeAsync(keys_tmp, st));
+  CPD_CUDA(h, cudaFreeAsync(perm, st));
+  CPD_CUDA(h, cudaFreeAsync(perm_tmp, st));
+  CPD_CUDA(h, cudaFreeAsync(flags, st));
+  CPD_CUDA(h, cudaFreeAsync(fid, st));
+  CPD_CUDA(h, cudaMemcpyAsync(&hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPD_CUDA(h, cudaStreamSynchronize(st));
+  if (hs != 0) return cpd_fail(h, (cpd_status)hs, "layout build failed on the device");
+  return CPD_OK;
+}

@@ -1,0 +1,216 @@
+// Leverage-score samplers of the Khatri-Rao product U_{!=n}.
+//
+// CP-ARLS-LEV (Appendix A, Algorithms 2-3): per factor k the scores
+// ell_k[i] = U_k[i] G_k^+ U_k[i]^T and their running sums (the inverse-CDF
+// table); a draw picks i_k independently per factor k != n.  Scores and
+// running sums are float64 so the inverse CDF takes the same decisions as a
+// float64 statement of Algorithm 3 up to ties at the last bits.
+//
+// STS-CP (Sec. 4.1, Appendix B, Algorithms 4-5) lives in sts.cu.
+#include "common.cuh"
+#include <algorithm>
+#include <cstring>
+
+namespace {
+
+constexpr int LEV_THREADS = 256;
+
+// ell_i = || B u_i ||^2 with G_k^+ = B^T B (B lower triangular when G_k was
+// factored by Cholesky).  One row per thread; u_i in registers, B in shared
+// memory (every thread reads the same entry: broadcast).  Also writes the sum
+// of each block's 256 scores.
+template <int RB>
+__global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
+                                                          const double* __restrict__ B, const int* __restrict__ tri,
+                                                          double* __restrict__ ell, double* __restrict__ blk) {
+  extern __shared__ double Bs[];     // R x R
+  __shared__ double red[LEV_THREADS / 32];
+  const int t = threadIdx.x;
+  for (int e = t; e < R * R; e += LEV_THREADS) Bs[e] = B[e];
+  const bool lower = *tri != 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * LEV_THREADS + t;
+  double l = 0.0;
+  if (i < I) {
+    float u[RB];
+    const float4* row = reinterpret_cast<const float4*>(U + i * Rp);
+#pragma unroll
+    for (int q = 0; q < RB / 4; ++q) {
+      if (4 * q < Rp) {
+        float4 v = row[q];
+        u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
+      } else {
+        u[4 * q] = u[4 * q + 1] = u[4 * q + 2] = u[4 * q + 3] = 0.0f;
+      }
+    }
+    if (lower) {
+#pragma unroll
+      for (int a = 0; a < RB; ++a) {
+        if (a < R) {
+          double y = 0.0;
+#pragma unroll
+          for (int b = 0; b <= a; ++b) y = fma(Bs[a * R + b], (double)u[b], y);
+          l = fma(y, y, l);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int a = 0; a < R; ++a) {
+        double y = 0.0;
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+          if (b < R) y = fma(Bs[a * R + b], (double)u[b], y);
+        l = fma(y, y, l);
+      }
+    }
+    ell[i] = l;
+  }
+  // block sum in a fixed order
+  double s = warp_sum(l);
+  if ((t & 31) == 0) red[t >> 5] = s;
+  __syncthreads();
+  if (t == 0) {
+    double b = 0.0;
+    for (int w = 0; w < LEV_THREADS / 32; ++w) b += red[w];
+    blk[blockIdx.x] = b;
+  }
+}
+
+// Exclusive scan of the block sums by one warp, fixed order: lane l owns a
+// contiguous run of the sums, the run totals are scanned with shuffles.
+__global__ void blk_scan_kernel(double* __restrict__ blk, int64_t nb) {
+  const int lane = threadIdx.x;
+  const int64_t per = (nb + 31) / 32;
+  const int64_t b0 = lane * per;
+  double s = 0.0;
+  for (int64_t q = 0; q < per; ++q)
+    if (b0 + q < nb) s += blk[b0 + q];
+  double x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double y = __shfl_up_sync(CPD_FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  double run = x - s;
+  for (int64_t q = 0; q < per; ++q)
+    if (b0 + q < nb) { double v = blk[b0 + q]; blk[b0 + q] = run; run += v; }
+}
+
+// cdf[i] = offset of the block + inclusive scan of the block's scores.
+__global__ void __launch_bounds__(LEV_THREADS) cdf_kernel(const double* __restrict__ ell, int64_t I,
+                                                          const double* __restrict__ blk, double* __restrict__ cdf) {
+  __shared__ double wsum[LEV_THREADS / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t i = (int64_t)blockIdx.x * LEV_THREADS + t;
+  double v = i < I ? ell[i] : 0.0;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double y = __shfl_up_sync(CPD_FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  double base = blk[blockIdx.x];
+  for (int q = 0; q < w; ++q) base += wsum[q];
+  if (i < I) cdf[i] = base + x;
+}
+
+struct DrawArgs {
+  const double* cdf[CPD_MAX_MODES];
+  const double* ell[CPD_MAX_MODES];
+  int64_t dims[CPD_MAX_MODES];
+  int N, n;
+  unsigned long long seed;
+};
+
+// Algorithm 3 with one processor: per factor k != n, i_k = smallest i with
+// cdf_k[i] > u * C_k (past the end: last row of nonzero score).
+__global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long* __restrict__ d_sweep,
+                                 unsigned long long h_sweep, int32_t* __restrict__ out_idx,
+                                 double* __restrict__ out_p, double* __restrict__ out_w) {
+  const unsigned long long s = d_sweep ? *d_sweep : h_sweep;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
+    double p = 1.0;
+    for (int k = 0; k < a.N; ++k) {
+      if (k == a.n) { out_idx[(int64_t)k * J + j] = -1; continue; }
+      const double* cdf = a.cdf[k];
+      const int64_t I = a.dims[k];
+      const double C = cdf[I - 1];
+      const double t = cpd_uniform(a.seed, CPD_STREAM_ARLS, (unsigned long long)j, (unsigned long long)k,
+                                   (unsigned long long)a.n, s) * C;
+      int64_t lo = 0, hi = I;           // first index in [lo, hi) with cdf > t
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+      }
+      if (lo >= I) {
+        lo = I - 1;
+        while (lo > 0 && !(a.ell[k][lo] > 0.0)) --lo;
+      }
+      out_idx[(int64_t)k * J + j] = (int32_t)lo;
+      p *= a.ell[k][lo] / C;
+    }
+    if (out_p) out_p[j] = p;
+    if (out_w) out_w[j] = 1.0 / ((double)J * p);
+  }
+}
+
+template <int RB>
+cpd_status launch_lev(cpd_ctx* h, int k) {
+  const int64_t I = h->dims[k];
+  const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
+  size_t shm = (size_t)h->R * h->R * sizeof(double);
+  lev_kernel<RB><<<(unsigned)nb, LEV_THREADS, shm, h->stream>>>(h->U[k], I, h->R, h->Rp, h->Bk[k], h->Btri + k,
+                                                                 h->ell[k], h->blk[k]);
+  CPD_LAUNCH(h, "lev");
+  blk_scan_kernel<<<1, 32, 0, h->stream>>>(h->blk[k], nb);
+  cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(h->ell[k], I, h->blk[k], h->cdf[k]);
+  CPD_LAUNCH(h, "cdf");
+  return CPD_OK;
+}
+
+}  // namespace
+
+// Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
+// once, outside any stream capture).
+cpd_status cpd_sample_init(cpd_ctx* h) {
+  int shm = h->R * h->R * (int)sizeof(double);
+  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  return CPD_OK;
+}
+
+cpd_status cpd_sts_refresh(cpd_ctx* h, int mode);
+cpd_status cpd_sts_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep,
+                        unsigned long long sweep, int32_t* out_idx, double* out_p, double* out_w);
+
+// Algorithm 2 (CP-ARLS-LEV build) or Algorithm 4 (STS-CP build) for factor
+// `mode`, from its current U and Gram.
+cpd_status cpd_refresh_sampler(cpd_ctx* h, int k) {
+  if (h->opt.method == CPD_STS_CP) return cpd_sts_refresh(h, k);
+  if (h->opt.method != CPD_ARLS_LEV) return CPD_OK;
+  cpd_status s = cpd_pinv_into(h, h->G[k], h->Gkpinv[k], h->Bk[k], h->Btri + k);
+  if (s != CPD_OK) return s;
+  const int R = h->R;
+  if (R <= 32) return launch_lev<32>(h, k);
+  if (R <= 64) return launch_lev<64>(h, k);
+  if (R <= 96) return launch_lev<96>(h, k);
+  return launch_lev<128>(h, k);
+}
+
+cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep, unsigned long long sweep,
+                    int32_t* out_idx, double* out_p, double* out_w) {
+  if (h->opt.method == CPD_STS_CP) return cpd_sts_draw(h, mode, J, d_sweep, sweep, out_idx, out_p, out_w);
+  DrawArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int k = 0; k < h->N; ++k) { a.cdf[k] = h->cdf[k]; a.ell[k] = h->ell[k]; a.dims[k] = h->dims[k]; }
+  a.N = h->N; a.n = mode; a.seed = h->opt.seed;
+  if (J <= 0) return CPD_OK;
+  int grid = (int)std::min<int64_t>(cpd_ceil_div(J, 256), (int64_t)h->num_sms * 8);
+  arls_draw_kernel<<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
+  CPD_LAUNCH(h, "arls_draw");
+  return CPD_OK;
+}

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: sample indices exact except draws the oracle marks as ties
+within 1e-12 of a bin boundary; draw probabilities 1e-12 relative (float64
+on both sides); sampled and exact MTTKRP 1e-5 relative Frobenius (float32
+accumulation); solve / renormalisation 1e-5; fit 1e-9 absolute for a given
+model and 1e-3 between full randomized runs.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cpals as oc
+from tests.gpu_common import cuda_ready, lib_or_build, make_case, create, gpu_factors, rel_frob
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ready(), reason="needs a CUDA GPU")]
+
+SMALL = dict(dims=(200, 150, 100), nnz=20000, R=8, J=2000)
+
+
+@pytest.fixture(scope="module")
+def cpd():
+    return lib_or_build()
+
+
+def _small(cpd, method="arls", **kw):
+    cfg = dict(SMALL)
+    cfg.update(kw)
+    idx, vals, init = make_case(cfg["dims"], cfg["nnz"], cfg["R"], seed=cfg.get("seed", 1001),
+                                zipf=cfg.get("zipf", 0.0))
+    h = create(cpd, cfg["dims"], idx, vals, init, method, cfg["R"], cfg["J"], seed=3001,
+               leaf_rows=cfg.get("F", 0))
+    return h, idx, vals, init, cfg
+
+
+def test_create_normalises_and_grams(cpd):
+    h, idx, vals, init, cfg = _small(cpd)
+    fs = gpu_factors(cpd, h)
+    for k in range(3):
+        ref = oc.renormalize(init[k].astype(np.float64))
+        assert rel_frob(fs[k], ref) < 1e-6
+        G = cpd.cpd_get_gram(h, k).cpu().numpy()
+        assert rel_frob(G, oc.gram(fs[k])) < 1e-13
+    h.close()
+
+
+def test_arls_sampler_state_matches_oracle(cpd):
+    h, idx, vals, init, cfg = _small(cpd)
+    fs = gpu_factors(cpd, h)
+    for k in range(3):
+        st = oc.arls_build(fs[k])
+        ell, cdf = cpd.cpd_get_arls_state(h, k)
+        assert np.max(np.abs(ell.cpu().numpy() - st["ell"]) / st["ell"].max()) < 1e-12
+        assert np.max(np.abs(cdf.cpu().numpy() - st["cdf"])) < 1e-12 * st["C"]
+        assert abs(st["C"] - cfg["R"]) < 1e-9           # leverage scores sum to R (Eq. 8)
+    h.close()
+
+
+@pytest.mark.parametrize("mode,sweep", [(0, 0), (1, 3), (2, 7)])
+def test_arls_draws_match_oracle_exactly(cpd, mode, sweep):
+    h, idx, vals, init, cfg = _small(cpd, J=20000)
+    fs = gpu_factors(cpd, h)
+    samplers = [oc.arls_build(U) for U in fs]
+    gi, gp = cpd.cpd_leverage_sample(h, mode, cfg["J"], sweep)
+    oi, op, near = oc.arls_draw(samplers, mode, cfg["J"], 3001, sweep)
+    gi = gi.cpu().numpy()
+    mism = np.any(gi != oi, axis=0)
+    assert not np.any(mism & ~near), "index mismatch away from a tie"
+    assert np.all(gi[mode] == -1)
+    ok = ~mism
+    assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-12
+    h.close()
+
+
+def _oracle_samples(fs, mode, J, seed, sweep):
+    samplers = [oc.arls_build(U) for U in fs]
+    oi, op, _ = oc.arls_draw(samplers, mode, J, seed, sweep)
+    return oi, op
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sampled_mttkrp_matches_oracle(cpd, mode):
+    h, idx, vals, init, cfg = _small(cpd, J=5000)
+    fs = gpu_factors(cpd, h)
+    oi, op = _oracle_samples(fs, mode, cfg["J"], 11, 0)
+    w = 1.0 / (cfg["J"] * op)
+    Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, torch.from_numpy(oi), torch.from_numpy(w))
+    ref = oc.sampled_mttkrp(idx, vals, cfg["dims"], fs, mode, oi, w)
+    assert rel_frob(Y.cpu().numpy(), ref) <= 1e-5
+    assert nsel == oc.selected_nnz(idx, cfg["dims"], mode, oi)
+    h.close()
+
+
+def test_sampled_mttkrp_edge_cases(cpd):
+    h, idx, vals, init, cfg = _small(cpd)
+    fs = gpu_factors(cpd, h)
+    dims = cfg["dims"]
+    # J = 0: Y = 0
+    Y, nsel = cpd.cpd_sampled_mttkrp(h, 0, torch.zeros((3, 0), dtype=torch.int32), torch.zeros(0, dtype=torch.float64))
+    assert nsel == 0 and float(Y.abs().max()) == 0.0
+    # one draw repeated, and a column with no nonzeros
+    e0 = idx[:, 0]
+    sidx = np.array([[-1, -1, -1, -1], [e0[1]] * 3 + [0], [e0[2]] * 3 + [0]], dtype=np.int64)
+    keys = oc.krp_key(idx, dims, 0)
+    empty_key = oc.krp_key(np.array([[0], [0], [0]]), dims, 0)[0]
+    w = np.array([0.5, 0.25, 2.0, 1.0])
+    Y, nsel = cpd.cpd_sampled_mttkrp(h, 0, torch.from_numpy(sidx), torch.from_numpy(w))
+    ref = oc.sampled_mttkrp(idx, vals, dims, fs, 0, sidx, w)
+    assert rel_frob(Y.cpu().numpy(), ref) <= 1e-5
+    assert nsel == oc.selected_nnz(idx, dims, 0, sidx)
+    assert nsel == np.count_nonzero(keys == keys[0]) + np.count_nonzero(keys == empty_key)
+    h.close()
+
+
+def test_exact_mttkrp_matches_oracle(cpd):
+    h, idx, vals, init, cfg = _small(cpd, method="exact")
+    fs = gpu_factors(cpd, h)
+    for mode in range(3):
+        Y = cpd.cpd_exact_mttkrp(h, mode)
+        assert rel_frob(Y.cpu().numpy(), oc.exact_mttkrp(idx, vals, cfg["dims"], fs, mode)) <= 1e-5
+    h.close()
+
+
+def test_gram_solve_matches_oracle(cpd):
+    h, idx, vals, init, cfg = _small(cpd)
+    fs = gpu_factors(cpd, h)
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((cfg["dims"][1], cfg["R"])).astype(np.float32)
+    sigma = cpd.cpd_gram_solve(h, 1, torch.from_numpy(Y)).cpu().numpy()
+    G = oc.hadamard_of_grams([oc.gram(U) for U in fs], 1)
+    U_ref, s_ref = oc.solve_and_renorm(Y.astype(np.float64), oc.pinv_sym(G))
+    U_g = cpd.cpd_get_factors(h, 1).double().cpu().numpy()
+    assert rel_frob(sigma, s_ref) < 1e-5
+    assert rel_frob(U_g, U_ref) < 1e-5
+    G1 = cpd.cpd_get_gram(h, 1).cpu().numpy()
+    assert rel_frob(G1, oc.gram(U_g)) < 1e-13
+    # the ARLS sampler of mode 1 was rebuilt from the new factor
+    ell, _ = cpd.cpd_get_arls_state(h, 1)
+    assert np.max(np.abs(ell.cpu().numpy() - oc.arls_build(U_g)["ell"])) < 1e-12 * cfg["R"]
+    h.close()
+
+
+def test_fit_matches_oracle(cpd):
+    h, idx, vals, init, cfg = _small(cpd)
+    cpd.cpd_als_sweep(h, 2)
+    f = cpd.cpd_fit(h)
+    fs = gpu_factors(cpd, h)
+    sigma = cpd.cpd_get_sigma(h).cpu().numpy()
+    assert abs(f - oc.fit(idx, vals, fs, sigma)) < 1e-9
+    h.close()
+
+
+def test_stepwise_sweep_matches_oracle(cpd):
+    """Teacher-forced: each mode update starts from the GPU's factors."""
+    h, idx, vals, init, cfg = _small(cpd)
+    J = cfg["J"]
+    for s in range(2):
+        for n in range(3):
+            fs = gpu_factors(cpd, h)
+            samplers = [oc.arls_build(U) for U in fs]
+            oi, op, near = oc.arls_draw(samplers, n, J, 3001, s)
+            gi, gp = cpd.cpd_leverage_sample(h, n, J, s)
+            gi = gi.cpu().numpy()
+            assert not np.any(np.any(gi != oi, axis=0) & ~near)
+            w = 1.0 / (J * gp.cpu().numpy())
+            Y, _ = cpd.cpd_sampled_mttkrp(h, n, torch.from_numpy(gi), torch.from_numpy(w))
+            Yo = oc.sampled_mttkrp(idx, vals, cfg["dims"], fs, n, gi, w)
+            assert rel_frob(Y.cpu().numpy(), Yo) <= 1e-5
+            cpd.cpd_gram_solve(h, n, Y)
+            Uo, _ = oc.solve_and_renorm(Y.double().cpu().numpy(),
+                                        oc.pinv_sym(oc.hadamard_of_grams([oc.gram(U) for U in fs], n)))
+            assert rel_frob(cpd.cpd_get_factors(h, n).double().cpu().numpy(), Uo) < 1e-5
+    h.close()
+
+
+def test_graph_sweep_equals_stepwise(cpd):
+    """cpd_als_sweep (captured graph) performs the same updates as the
+    step-wise entry points with sweep counter 0, 1, ..."""
+    h1, idx, vals, init, cfg = _small(cpd)
+    h2, *_ = _small(cpd)
+    J = cfg["J"]
+    cpd.cpd_als_sweep(h1, 2)
+    for s in range(2):
+        for n in range(3):
+            gi, gp = cpd.cpd_leverage_sample(h2, n, J, s)
+            w = 1.0 / (J * gp)
+            Y, _ = cpd.cpd_sampled_mttkrp(h2, n, gi, w)
+            cpd.cpd_gram_solve(h2, n, Y)
+    for k in range(3):
+        assert rel_frob(cpd.cpd_get_factors(h1, k).cpu().numpy(), cpd.cpd_get_factors(h2, k).cpu().numpy()) < 1e-4
+    h1.close()
+    h2.close()
+
+
+def test_end_to_end_fit_small_uniform(cpd):
+    """200x150x100, 20k uniform nonzeros, R = 8, J = 2000, 5 sweeps of
+    CP-ARLS-LEV: final fit within 1e-3 of the oracle's own run."""
+    h, idx, vals, init, cfg = _small(cpd)
+    cpd.cpd_als_sweep(h, 5)
+    f_gpu = cpd.cpd_fit(h)
+    _, fits = oc.als(idx, vals, cfg["dims"], [u.astype(np.float64) for u in init], "arls", 5, J=cfg["J"], seed=3001)
+    assert abs(f_gpu - fits[-1]) < 1e-3
+    h.close()
+
+
+def test_host_input_matches_device_input(cpd):
+    cfgd = SMALL
+    idx, vals, init = make_case(cfgd["dims"], cfgd["nnz"], cfgd["R"], seed=1001)
+    h1 = create(cpd, cfgd["dims"], idx, vals, init, "arls", cfgd["R"], cfgd["J"], seed=3001)
+    h2 = create(cpd, cfgd["dims"], idx, vals, init, "arls", cfgd["R"], cfgd["J"], seed=3001, on_host=True)
+    for k in range(3):
+        assert torch.equal(cpd.cpd_get_factors(h1, k), cpd.cpd_get_factors(h2, k))
+    h1.close()
+    h2.close()
+
+
+def test_rank_deficient_gram_uses_pseudo_inverse(cpd):
+    """R > I_0 makes G_0 singular: the Jacobi pseudo-inverse path must give
+    the oracle's leverage scores (they sum to rank = I_0)."""
+    dims = (5, 60, 40)
+    idx, vals, init = make_case(dims, 3000, 8, seed=77)
+    h = create(cpd, dims, idx, vals, init, "arls", 8, 500, seed=5)
+    fs = gpu_factors(cpd, h)
+    st = oc.arls_build(fs[0])
+    ell, cdf = cpd.cpd_get_arls_state(h, 0)
+    assert abs(st["C"] - 5.0) < 1e-9
+    assert np.max(np.abs(ell.cpu().numpy() - st["ell"])) < 1e-9
+    h.close()
+
+
+def test_odd_rank_and_ragged_tiles(cpd):
+    """R = 25 (not a multiple of 4) and modes that are not tile multiples."""
+    dims = (333, 97, 1031)
+    idx, vals, init = make_case(dims, 30000, 25, seed=90)
+    h = create(cpd, dims, idx, vals, init, "arls", 25, 3000, seed=9)
+    fs = gpu_factors(cpd, h)
+    for k in range(3):
+        assert rel_frob(cpd.cpd_get_gram(h, k).cpu().numpy(), oc.gram(fs[k])) < 1e-13
+    oi, op = _oracle_samples(fs, 2, 3000, 9, 0)
+    gi, gp = cpd.cpd_leverage_sample(h, 2, 3000, 0)
+    w = 1.0 / (3000 * op)
+    Y, _ = cpd.cpd_sampled_mttkrp(h, 2, torch.from_numpy(oi), torch.from_numpy(w))
+    assert rel_frob(Y.cpu().numpy(), oc.sampled_mttkrp(idx, vals, dims, fs, 2, oi, w)) <= 1e-5
+    cpd.cpd_als_sweep(h, 1)
+    fs2 = gpu_factors(cpd, h)
+    f = cpd.cpd_fit(h)
+    assert abs(f - oc.fit(idx, vals, fs2, cpd.cpd_get_sigma(h).cpu().numpy())) < 1e-9
+    h.close()
+
+
+def test_invalid_inputs_are_reported(cpd):
+    dims = (10, 10, 10)
+    idx, vals, init = make_case(dims, 100, 4, seed=3)
+    bad = idx.copy()
+    bad[1, 5] = 10                     # out of range
+    with pytest.raises(cpd.CpdError) as e:
+        create(cpd, dims, bad, vals, init, "arls", 4, 10, seed=1)
+    assert e.value.status == 2
+    dup = idx.copy()
+    dup[:, 7] = dup[:, 3]              # duplicate coordinate
+    with pytest.raises(cpd.CpdError) as e:
+        create(cpd, dims, dup, vals, init, "arls", 4, 10, seed=1)
+    assert e.value.status == 3
+    h = create(cpd, dims, idx, vals, init, "arls", 4, 10, seed=1)
+    sidx = np.zeros((3, 4), dtype=np.int64)
+    sidx[2, 1] = 99                    # out-of-range draw: latched, reported
+    with pytest.raises(cpd.CpdError) as e:
+        cpd.cpd_sampled_mttkrp(h, 0, torch.from_numpy(sidx), torch.ones(4, dtype=torch.float64))
+    assert e.value.status == 2
+    # the handle stays usable afterwards
+    Y, _ = cpd.cpd_sampled_mttkrp(h, 0, torch.zeros((3, 4), dtype=torch.int32), torch.ones(4, dtype=torch.float64))
+    h.close()
