@@ -1,0 +1,377 @@
+"""Benchmark: randomized CP-ALS sweeps per second on one GB300 (or N replicas).
+
+Workload (default): 3-mode tensor 100,000^3 with 50M distinct nonzeros, mode
+indices Zipf(s = 1.1), values lognormal(0, 1), R = 32, J = 65,536,
+CP-ARLS-LEV (or STS-CP with --method sts), float32 factors with float64
+Grams, leverage scores and R x R algebra.  Data is synthetic and seeded.
+
+A step is one ALS round (Algorithm 1: every mode sampled, MTTKRP'd, solved),
+replayed from a captured CUDA graph with inputs resident in HBM.  Between
+timed steps L2 is flushed (a 256 MB write), outside the events.
+
+Also reported on the same JSON line: end-to-end sweeps/s through the C ABI
+from host buffers (cpd_create from pinned host COO, the sweeps, fit, factors
+back to the host), the roofline of the dominant kernel, the FP64 oracle timed
+on the host (cpu_baseline), a per-phase breakdown, clocks during the timed
+region and the kernel-launch count.
+
+--impl reference times the FP64 oracle on the host cores instead (each step
+one mode update of the same workload).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2210_05105_gb300 import synth
+
+METRIC = "ALS sweeps/s"
+FALLBACK_HBM = 6800.0
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 FP64 FMA / clock / SM at 2070 MHz
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--method", default="arls", choices=["arls", "sts"])
+    p.add_argument("--workload", default="zipf_1e5cube_50M", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_worker(path):
+    """Time the FP64 oracle: one ALS round (N mode updates) of the workload."""
+    from oracle import cpals as oc
+    d = np.load(path, allow_pickle=True)
+    meta = json.loads(str(d["meta"]))
+    idx, vals = d["idx"], d["vals"]
+    init = [d["init%d" % k] for k in range(len(meta["dims"]))]
+    modes = meta.get("modes", list(range(len(meta["dims"]))))
+    state = oc.als_init(idx, vals, meta["dims"], [u.astype(np.float64) for u in init], meta["method"])
+    t0 = time.perf_counter()
+    for n in modes:
+        oc.als_mode_update(state, n, meta["method"], meta["J"], meta["seed"], 0)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "mode_updates": len(modes)}))
+
+
+def run_oracle(idx, vals, init, w, method, modes, threads=1):
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "case.npz")
+        meta = {"dims": list(w["dims"]), "J": w["J"], "seed": w["sample_seed"], "method": method, "modes": modes}
+        np.savez(path, idx=idx, vals=vals, meta=json.dumps(meta), **{"init%d" % k: u for k, u in enumerate(init)})
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", path], env=env,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr[-2000:])
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------ byte models
+def algorithmic(phase, w, stats):
+    """Algorithmic bytes (or FP64 flops) per launch of a phase's kernel."""
+    N, R, J = len(w["dims"]), w["R"], w["J"]
+    Rp = (R + 3) // 4 * 4
+    if phase == "spmm":
+        # selected (row, value) pairs, weight + offsets per distinct column,
+        # its KRP row, one write of every touched output row
+        return "hbm", stats["nnz_sel"] * 8 + stats["J_u"] * (R * 4 + 16) + stats["rows"] * R * 4
+    if phase == "probe":
+        return "hbm", J * (N - 1) * 4 + J * 8 + stats["J_u"] * ((N - 1) * R * 4 + R * 4) + J * 16
+    if phase in ("sampler", "gram"):
+        I = stats["I_mean"]
+        return "alu", I * R * (R + 1) / 2 * 2   # FP64 flops of the quadratic forms / Gram pairs
+    if phase == "solve":
+        I = stats["I_mean"]
+        return "hbm", I * Rp * 4 * 2
+    return "hbm", 0
+
+
+def ours(args, world, rank, local):
+    import torch
+    from paper_2210_05105_gb300 import cpd
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    w = synth.WORKLOADS[args.workload]
+    dims, R, J = w["dims"], w["R"], w["J"]
+    N = len(dims)
+    idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
+    init_np = synth.init_factors(dims, R, w["init_seed"])
+    init = [torch.from_numpy(u).cuda() for u in init_np]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"])
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+
+    cpd.cpd_als_sweep(h, args.warmup)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = Clocks(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        cpd.cpd_als_sweep(h, 1, sync=False)
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    total_ms = allreduce_max(sum(step_ms), world)
+    value = world * args.steps / (total_ms / 1e3)
+    launches_per_step = cpd.cpd_sweep_kernel_count(h)
+    fit = cpd.cpd_fit(h)
+
+    # per-phase breakdown of one round, step-wise entry points (same kernels)
+    sweep_id = args.warmup + args.steps
+    cpd.cpd_profile(h, True)
+    stats = {"nnz_sel": 0, "J_u": 0, "rows": 0, "I_mean": sum(dims) / N}
+    spmm_ms_list = []
+    for n in range(N):
+        gi, gp = cpd.cpd_leverage_sample(h, n, J, sweep_id)
+        wts = 1.0 / (J * gp)
+        before = cpd.cpd_profile_read(h)
+        Y, nsel = cpd.cpd_sampled_mttkrp(h, n, gi, wts)
+        ph = cpd.cpd_profile_read(h)
+        spmm_ms_list.append(ph["spmm"][0])
+        for k, v in before.items():
+            ph[k] = (ph[k][0] + v[0], ph[k][1] + v[1])
+        cpd.cpd_gram_solve(h, n, Y)
+        ph2 = cpd.cpd_profile_read(h)
+        for k in ph:
+            ph[k] = (ph[k][0] + ph2[k][0], ph[k][1] + ph2[k][1])
+        stats.setdefault("phases", []).append(ph)
+        keys = torch.zeros(J, dtype=torch.int64, device="cuda")
+        mult = 1
+        for k in range(N):
+            if k != n:
+                keys += gi[k].long() * mult
+                mult *= dims[k]
+        stats["nnz_sel"] += nsel
+        stats["J_u"] += int(torch.unique(keys).numel())
+        stats["rows"] += int((Y != 0).any(dim=1).sum())
+    cpd.cpd_profile(h, False)
+    phases = {}
+    for ph in stats["phases"]:
+        for k, (ms, n_) in ph.items():
+            a, b = phases.get(k, (0.0, 0))
+            phases[k] = (a + ms, b + n_)
+    for k in ("nnz_sel", "J_u", "rows"):
+        stats[k] = stats[k] / N          # per mode update
+    dominant = max((k for k in phases if phases[k][1] > 0), key=lambda k: phases[k][0])
+    hbm_peak, peak_kind = peaks()
+
+    def roof(phase):
+        ms, n_ = phases[phase]
+        per_launch_ms = ms / max(n_, 1)
+        bound, amount = algorithmic(phase, w, stats)
+        if bound == "alu":
+            ach = amount / (per_launch_ms / 1e3) / 1e12
+            return {"phase": phase, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": "derived FP64 FMA rate"}
+        ach = amount / (per_launch_ms / 1e3) / 1e9
+        return {"phase": phase, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind}
+
+    roofline = roof(dominant)
+    roofline_spmm = roof("spmm")
+
+    # end-to-end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        idx_h = idx.cpu().pin_memory()
+        vals_h = vals.cpu().pin_memory()
+        init_h = [u.cpu().pin_memory() for u in init]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = cpd.cpd_create(dims, idx_h, vals_h, init_h, method=args.method, rank=R, samples=J, seed=w["sample_seed"])
+        cpd.cpd_als_sweep(h2, args.steps, sync=False)
+        f2 = cpd.cpd_fit(h2)
+        outs = [cpd.cpd_get_factors(h2, k, out=torch.empty((dims[k], R), dtype=torch.float32).pin_memory())
+                for k in range(N)]
+        e2e_s = time.perf_counter() - t0
+        h2.close()
+        h2d = idx_h.numel() * 4 + vals_h.numel() * 4 + sum(u.numel() * 4 for u in init_h)
+        d2h = sum(o.numel() * 4 for o in outs) + 8
+        e2e_s = allreduce_max(e2e_s, world)
+        e2e = {"value": world * args.steps / e2e_s, "unit": "sweeps/s", "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps, "job": "cpd_create(host COO) + %d sweeps + fit + factors to host"
+               % args.steps, "job_seconds": e2e_s, "fit": f2}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
+        res = run_oracle(idx_np, vals_np, init_np, w, args.method, list(range(N)))
+        cpu = {"value": (res["mode_updates"] / N) / res["seconds"], "unit": "sweeps/s", "cores": 1,
+               "kind": "oracle", "sample": "one ALS round (all %d mode updates) of the full workload, FP64 numpy, "
+                                          "1 thread, from the initial factors" % N, "seconds": res["seconds"]}
+    h.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": args.workload, "dims": list(dims), "nnz": w["nnz"], "zipf_s": w["zipf"],
+                           "values": w["values"], "R": R, "J": J, "method": args.method,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed between steps (256 MB write, outside the events)",
+                           "create_seconds": create_s},
+                "roofline": roofline, "roofline_spmm": roofline_spmm, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+                "phases_ms_per_sweep": {k: round(v[0], 4) for k, v in phases.items() if v[1]},
+                "mttkrp_stats_per_mode": {k: stats[k] for k in ("nnz_sel", "J_u", "rows")},
+                "fit": fit, "step_ms_median": statistics.median(step_ms)}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def reference(args, world, rank, local):
+    """FP64 oracle on the host cores, each step one mode update."""
+    if rank != 0:
+        return
+    import torch
+    w = synth.WORKLOADS[args.workload]
+    dims = w["dims"]
+    N = len(dims)
+    if torch.cuda.is_available():
+        idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
+        idx, vals = idx.cpu().numpy(), vals.cpu().numpy()
+    else:
+        idx, vals = synth.make_tensor(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"])
+    init = synth.init_factors(dims, w["R"], w["init_seed"])
+    modes_w = [k % N for k in range(args.warmup)]
+    modes_t = [k % N for k in range(args.steps)]
+    if modes_w:
+        run_oracle(idx, vals, init, w, args.method, modes_w)
+    res = run_oracle(idx, vals, init, w, args.method, modes_t)
+    value = (len(modes_t) / N) / res["seconds"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["seconds"] * 1e3 / max(len(modes_t), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "dims": list(dims), "nnz": w["nnz"], "R": w["R"], "J": w["J"],
+                       "method": args.method, "step": "one mode update of the FP64 oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value,
+                             "sample": "%d mode updates of the full workload, FP64 numpy, 1 thread" % len(modes_t)},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker)
+        return
+    world, rank, local = dist()
+    if args.impl == "reference":
+        reference(args, world, rank, local)
+    else:
+        ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,34 @@ cpd_status cpd_get_arls_state(cpd_handle h, int32_t mode, double* ell, double* c
 /* Copy the Gram U_mode^T U_mode (R x R float64).  Synchronises. */
 cpd_status cpd_get_gram(cpd_handle h, int32_t mode, double* dst);
 
+/*
+ * Phase timers (profiling aid; the paper's runtime breakdown of Sec. 5 into
+ * sampling, MTTKRP and post-processing).  While enabled, step-wise entry
+ * points bracket each kernel class with CUDA events on the handle's stream;
+ * captured sweeps (cpd_als_sweep) are not timed.  cpd_profile_read
+ * synchronises, returns the accumulated milliseconds and launch counts per
+ * phase (arrays of CPD_NUM_PHASES, either may be NULL) and clears them.
+ */
+typedef enum {
+  CPD_PHASE_PINV = 0,      /* Hadamard of Grams and pseudo-inverse */
+  CPD_PHASE_DRAW = 1,      /* leverage-score draws */
+  CPD_PHASE_PROBE = 2,     /* sampled MTTKRP: hash lookup, merge, KRP rows */
+  CPD_PHASE_SCAN = 3,      /* sampled MTTKRP: offsets of selected nonzeros */
+  CPD_PHASE_SPMM = 4,      /* sampled MTTKRP: accumulation into Y */
+  CPD_PHASE_SOLVE = 5,     /* Y G^+ and column norms */
+  CPD_PHASE_GRAM = 6,      /* renormalisation and Gram */
+  CPD_PHASE_SAMPLER = 7,   /* sampler rebuild (leverage + CDF, or tree) */
+  CPD_PHASE_EXACT = 8,     /* exact MTTKRP */
+  CPD_PHASE_CLEAR = 9,     /* clearing Y and per-call tables */
+  CPD_NUM_PHASES = 10
+} cpd_phase;
+cpd_status cpd_profile(cpd_handle h, int32_t enable);
+cpd_status cpd_profile_read(cpd_handle h, double* ms, int64_t* launches);
+
+/* Number of kernel launches in one captured ALS round (0 before the first
+ * cpd_als_sweep); memset and event nodes are not counted. */
+cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out);
+
 /* Wait for the handle's stream and return the first latched device error. */
 cpd_status cpd_synchronize(cpd_handle h);
 

@@ -19,7 +19,9 @@ STATUS = {0: "CPD_OK", 1: "CPD_ERR_INVALID_ARG", 2: "CPD_ERR_OUT_OF_RANGE_INDEX"
           8: "CPD_ERR_TIMEOUT", 9: "CPD_ERR_NOT_FINITE"}
 EXPORTS = ["cpd_default_options", "cpd_create", "cpd_leverage_sample", "cpd_sampled_mttkrp", "cpd_exact_mttkrp",
            "cpd_gram_solve", "cpd_als_sweep", "cpd_fit", "cpd_get_factors", "cpd_set_factors", "cpd_get_sigma",
-           "cpd_get_arls_state", "cpd_get_gram", "cpd_synchronize", "cpd_last_error", "cpd_destroy"]
+           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_synchronize",
+           "cpd_last_error", "cpd_destroy"]
+PHASES = ["pinv", "draw", "probe", "scan", "spmm", "solve", "gram", "sampler", "exact", "clear"]
 
 
 class cpd_options(ctypes.Structure):
@@ -61,6 +63,9 @@ def lib():
         "cpd_get_sigma": ([_P, _P], st),
         "cpd_get_arls_state": ([_P, i32, _P, _P], st),
         "cpd_get_gram": ([_P, i32, _P], st),
+        "cpd_profile": ([_P, i32], st),
+        "cpd_profile_read": ([_P, _P, _P], st),
+        "cpd_sweep_kernel_count": ([_P, _P], st),
         "cpd_synchronize": ([_P], st),
         "cpd_last_error": ([_P], ctypes.c_char_p),
         "cpd_destroy": ([_P], None),
@@ -211,6 +216,24 @@ def cpd_get_gram(h, mode):
     G = torch.empty((h.R, h.R), dtype=torch.float64, device=h.device)
     h._check(lib().cpd_get_gram(h.raw, mode, _ptr(G)))
     return G
+
+
+def cpd_profile(h, enable=True):
+    h._check(lib().cpd_profile(h.raw, 1 if enable else 0))
+
+
+def cpd_profile_read(h):
+    """-> {phase: (milliseconds, launches)} accumulated since the last read."""
+    ms = (ctypes.c_double * len(PHASES))()
+    n = (ctypes.c_int64 * len(PHASES))()
+    h._check(lib().cpd_profile_read(h.raw, ctypes.cast(ms, _P), ctypes.cast(n, _P)))
+    return {p: (ms[i], n[i]) for i, p in enumerate(PHASES)}
+
+
+def cpd_sweep_kernel_count(h):
+    n = ctypes.c_int64()
+    h._check(lib().cpd_sweep_kernel_count(h.raw, ctypes.cast(ctypes.byref(n), _P)))
+    return n.value
 
 
 def cpd_synchronize(h):

@@ -285,6 +285,8 @@ cpd_status cpd_als_sweep(cpd_handle h, int32_t n_sweeps) {
     // which cannot be captured), replay on the caller's
     CPD_CUDA(h, cudaStreamSynchronize(h->stream));
     cudaStream_t saved = h->stream;
+    const bool prof = h->profiling;
+    h->profiling = false;
     h->stream = h->cap_stream;
     cudaError_t eb = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (eb != cudaSuccess) { h->stream = saved; return cpd_cuda_check(h, eb, "cudaStreamBeginCapture"); }
@@ -292,6 +294,7 @@ cpd_status cpd_als_sweep(cpd_handle h, int32_t n_sweeps) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->stream = saved;
+    h->profiling = prof;
     if (s != CPD_OK) { if (g) cudaGraphDestroy(g); return s; }
     if (e != cudaSuccess) return cpd_cuda_check(h, e, "cudaStreamEndCapture");
     h->sweep_graph = g;
@@ -351,6 +354,60 @@ cpd_status cpd_get_gram(cpd_handle h, int32_t mode, double* dst) {
   return read_status(h);
 }
 
+static cpd_status drain_marks(cpd_ctx* h) {
+  if (h->marks.empty()) return CPD_OK;
+  CPD_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& m : h->marks) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      h->prof_ms[m.phase] += ms;
+      h->prof_n[m.phase] += 1;
+    }
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  h->marks.clear();
+  return CPD_OK;
+}
+
+cpd_status cpd_profile(cpd_handle h, int32_t enable) {
+  if (!h) return CPD_ERR_INVALID_ARG;
+  cpd_status s = drain_marks(h);
+  h->profiling = enable != 0;
+  return s;
+}
+
+cpd_status cpd_profile_read(cpd_handle h, double* ms, int64_t* launches) {
+  if (!h) return CPD_ERR_INVALID_ARG;
+  cpd_status s = drain_marks(h);
+  if (s != CPD_OK) return s;
+  for (int p = 0; p < CPD_NUM_PHASES; ++p) {
+    if (ms) ms[p] = h->prof_ms[p];
+    if (launches) launches[p] = h->prof_n[p];
+    h->prof_ms[p] = 0.0;
+    h->prof_n[p] = 0;
+  }
+  return CPD_OK;
+}
+
+cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out) {
+  if (!h || !out) return CPD_ERR_INVALID_ARG;
+  *out = 0;
+  if (!h->sweep_graph) return CPD_OK;
+  size_t n = 0;
+  CPD_CUDA(h, cudaGraphGetNodes(h->sweep_graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CPD_CUDA(h, cudaGraphGetNodes(h->sweep_graph, nodes.data(), &n));
+  int64_t k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CPD_CUDA(h, cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *out = k;
+  return CPD_OK;
+}
+
 cpd_status cpd_synchronize(cpd_handle h) {
   if (!h) return CPD_ERR_INVALID_ARG;
   return read_status(h);
@@ -364,6 +421,7 @@ const char* cpd_last_error(cpd_handle h) {
 void cpd_destroy(cpd_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (auto& m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
   if (h->sweep_graph) cudaGraphDestroy(h->sweep_graph);
   for (void* p : h->allocs) cudaFree(p);

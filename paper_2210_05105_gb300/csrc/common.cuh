@@ -102,6 +102,24 @@ struct cpd_ctx {
   unsigned long long host_sweep = 0;
 
   std::vector<void*> allocs;
+
+  // phase timers (cpd_profile)
+  bool profiling = false;
+  struct Mark { int phase; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  double prof_ms[CPD_NUM_PHASES] = {0};
+  int64_t prof_n[CPD_NUM_PHASES] = {0};
+};
+
+// Bracket the launches between begin/end with events when profiling.
+struct PhaseTimer {
+  cpd_ctx* h; int phase; cudaEvent_t a = nullptr, b = nullptr;
+  PhaseTimer(cpd_ctx* hh, int ph) : h(hh), phase(ph) {
+    if (h->profiling) { cudaEventCreate(&a); cudaEventCreate(&b); cudaEventRecord(a, h->stream); }
+  }
+  ~PhaseTimer() {
+    if (h->profiling) { cudaEventRecord(b, h->stream); h->marks.push_back({phase, a, b}); }
+  }
 };
 
 // ---- error helpers -------------------------------------------------------

@@ -439,6 +439,7 @@ __global__ void fit_final_kernel(const double* __restrict__ part, int nblk, FitA
 static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I, const double* sigma, int do_scale,
                             double* G) {
   const int R = h->R;
+  PhaseTimer pt(h, CPD_PHASE_GRAM);
   size_t shm = (size_t)TR * R * sizeof(double);
   normalize_gram_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
                                                                       h->Gpart);
@@ -466,6 +467,7 @@ cpd_status cpd_renormalize_inputs(cpd_ctx* h) {
 }
 
 static cpd_status launch_pinv(cpd_ctx* h, const PinvJobs& jobs, int njobs) {
+  PhaseTimer pt(h, CPD_PHASE_PINV);
   const int R = h->R;
   size_t shm = (size_t)R * R * sizeof(double);
   pinv_kernel<<<njobs, DTHREADS, shm, h->stream>>>(jobs, R);
@@ -502,11 +504,14 @@ cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P, double* B, int*
 cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_sigma) {
   const int R = h->R;
   const int64_t I = h->dims[mode];
-  size_t shm = (size_t)(2 * R * R + TR * R) * sizeof(float);
-  solve_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
-  CPD_LAUNCH(h, "solve");
-  sigma_kernel<<<1, 128, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
-  CPD_LAUNCH(h, "sigma");
+  {
+    PhaseTimer pt(h, CPD_PHASE_SOLVE);
+    size_t shm = (size_t)(2 * R * R + TR * R) * sizeof(float);
+    solve_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+    CPD_LAUNCH(h, "solve");
+    sigma_kernel<<<1, 128, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
+    CPD_LAUNCH(h, "sigma");
+  }
   if (out_sigma && out_sigma != h->sigma)
     CPD_CUDA(h, cudaMemcpyAsync(out_sigma, h->sigma, R * sizeof(double), cudaMemcpyDefault, h->stream));
   return gram_from(h, h->Uwork, h->U[mode], I, h->sigma, 1, h->G[mode]);

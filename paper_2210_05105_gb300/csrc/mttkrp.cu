@@ -232,25 +232,36 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
                                      int64_t J, float* Y, int64_t* out_nnz_sel) {
   (void)p;
   cudaStream_t st = h->stream;
-  CPD_CUDA(h, cudaMemsetAsync(Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), st));
-  CPD_CUDA(h, cudaMemsetAsync(h->dd_tag, 0xff, ((size_t)h->dedup_mask + 1) * sizeof(uint32_t), st));
-  CPD_CUDA(h, cudaMemsetAsync(h->dd_w, 0, ((size_t)h->dedup_mask + 1) * sizeof(double), st));
-  CPD_CUDA(h, cudaMemsetAsync(h->counters, 0, 4 * sizeof(uint32_t), st));
+  {
+    PhaseTimer pt(h, CPD_PHASE_CLEAR);
+    CPD_CUDA(h, cudaMemsetAsync(Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), st));
+    CPD_CUDA(h, cudaMemsetAsync(h->dd_tag, 0xff, ((size_t)h->dedup_mask + 1) * sizeof(uint32_t), st));
+    CPD_CUDA(h, cudaMemsetAsync(h->dd_w, 0, ((size_t)h->dedup_mask + 1) * sizeof(double), st));
+    CPD_CUDA(h, cudaMemsetAsync(h->counters, 0, 4 * sizeof(uint32_t), st));
+  }
   MArgs a = make_args(h, mode);
   if (J > 0) {
+    PhaseTimer pt(h, CPD_PHASE_PROBE);
     int grid = (int)std::min<int64_t>(cpd_ceil_div(J * 32, 256), (int64_t)h->num_sms * 16);
     probe_kernel<<<grid, 256, 0, st>>>(a, idx, w, J);
     CPD_LAUNCH(h, "probe");
   }
-  scan_kernel<<<1, 1024, 0, st>>>(a, out_nnz_sel);
-  CPD_LAUNCH(h, "scan");
-  spmm_kernel<<<h->num_sms * 8, 256, 0, st>>>(a, Y);
-  CPD_LAUNCH(h, "spmm");
+  {
+    PhaseTimer pt(h, CPD_PHASE_SCAN);
+    scan_kernel<<<1, 1024, 0, st>>>(a, out_nnz_sel);
+    CPD_LAUNCH(h, "scan");
+  }
+  {
+    PhaseTimer pt(h, CPD_PHASE_SPMM);
+    spmm_kernel<<<h->num_sms * 8, 256, 0, st>>>(a, Y);
+    CPD_LAUNCH(h, "spmm");
+  }
   return CPD_OK;
 }
 
 cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y) {
   cudaStream_t st = h->stream;
+  PhaseTimer pt(h, CPD_PHASE_EXACT);
   CPD_CUDA(h, cudaMemsetAsync(Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), st));
   if (h->nnz == 0) return CPD_OK;
   MArgs a = make_args(h, mode);

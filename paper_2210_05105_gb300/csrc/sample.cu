@@ -158,6 +158,7 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
 
 template <int RB>
 cpd_status launch_lev(cpd_ctx* h, int k) {
+  PhaseTimer pt(h, CPD_PHASE_SAMPLER);
   const int64_t I = h->dims[k];
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
   size_t shm = (size_t)h->R * h->R * sizeof(double);
@@ -209,6 +210,7 @@ cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d
   for (int k = 0; k < h->N; ++k) { a.cdf[k] = h->cdf[k]; a.ell[k] = h->ell[k]; a.dims[k] = h->dims[k]; }
   a.N = h->N; a.n = mode; a.seed = h->opt.seed;
   if (J <= 0) return CPD_OK;
+  PhaseTimer pt(h, CPD_PHASE_DRAW);
   int grid = (int)std::min<int64_t>(cpd_ceil_div(J, 256), (int64_t)h->num_sms * 8);
   arls_draw_kernel<<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
   CPD_LAUNCH(h, "arls_draw");

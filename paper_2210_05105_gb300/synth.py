@@ -106,3 +106,89 @@ WORKLOADS = {
                              values="lognormal", R=32, J=65536, sweeps=20,
                              data_seed=1002, init_seed=2002, sample_seed=3002),
 }
+
+
+def make_tensor_torch(dims, nnz, seed, zipf_s=0.0, values="uniform", device="cuda"):
+    """Device-side version of the same recipe for the large workloads (torch
+    generator on `device`, seeded): returns (idx (N, nnz) int32, vals (nnz,)
+    float32) torch tensors on `device`.  Exactly nnz distinct coordinates,
+    earliest draws kept."""
+    import torch
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    tables, perms = [], []
+    for I in dims:
+        if zipf_s:
+            r = torch.arange(1, I + 1, dtype=torch.float64, device=device)
+            c = torch.cumsum(r.pow(-float(zipf_s)), 0)
+            tables.append(c / c[-1])
+            perms.append(torch.randperm(I, generator=g, device=device))
+    one_key = True
+    total = 1
+    for d in dims:
+        total *= d
+    if total >= 2 ** 62:
+        one_key = False
+    mult = []
+    acc = 1
+    for d in dims:
+        mult.append(acc)
+        acc *= d
+
+    def draw(count):
+        cols = []
+        for k, I in enumerate(dims):
+            if zipf_s:
+                u = torch.rand(count, generator=g, device=device, dtype=torch.float64)
+                rank = torch.clamp(torch.searchsorted(tables[k], u, right=True), max=I - 1)
+                cols.append(perms[k][rank])
+            else:
+                cols.append(torch.randint(0, I, (count,), generator=g, device=device))
+        return torch.stack(cols)
+
+    drawn = torch.empty((N, 0), dtype=torch.int64, device=device)
+    need = nnz
+    while True:
+        drawn = torch.cat([drawn, draw(max(1024, int(need * 1.15) + 16))], dim=1)
+        if one_key:
+            key = torch.zeros(drawn.shape[1], dtype=torch.int64, device=device)
+            for k in range(N):
+                key += drawn[k] * mult[k]
+            _, inv = torch.unique(key, return_inverse=True)
+        else:
+            half = N // 2
+            k1 = torch.zeros(drawn.shape[1], dtype=torch.int64, device=device)
+            k2 = torch.zeros_like(k1)
+            a1 = a2 = 1
+            for k in range(half):
+                k1 += drawn[k] * a1
+                a1 *= dims[k]
+            for k in range(half, N):
+                k2 += drawn[k] * a2
+                a2 *= dims[k]
+            _, inv = torch.unique(torch.stack([k1, k2], dim=1), dim=0, return_inverse=True)
+        pos = torch.arange(drawn.shape[1], device=device)
+        first = torch.full((int(inv.max()) + 1,), drawn.shape[1], dtype=torch.int64, device=device)
+        first.scatter_reduce_(0, inv, pos, reduce="amin")
+        first, _ = torch.sort(first)
+        if first.numel() >= nnz:
+            idx = drawn[:, first[:nnz]].to(torch.int32).contiguous()
+            break
+        need = nnz - first.numel()
+        drawn = drawn[:, first]
+    if values == "uniform":
+        vals = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
+    elif values == "lognormal":
+        vals = torch.randn(nnz, generator=g, device=device, dtype=torch.float32).exp()
+    elif values == "logpoisson":
+        x = torch.poisson(torch.full((nnz,), 3.0, device=device), generator=g)
+        bad = x == 0
+        while bool(bad.any()):
+            x[bad] = torch.poisson(torch.full((int(bad.sum()),), 3.0, device=device), generator=g)
+            bad = x == 0
+        vals = torch.log1p(x).to(torch.float32)
+    else:
+        raise ValueError(values)
+    return idx, vals
