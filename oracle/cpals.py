@@ -285,13 +285,13 @@ def _sts_walk(tree, U, Ggt, h, u, tie_tol):
         return np.einsum("ja,jab,ab,jb->j", h, nodes[vs], Ggt, h)
 
     v = np.ones(m, dtype=np.int64)
-    t = u * mass(v)
+    mroot = mass(v)
+    t = u * mroot
     near = np.zeros(m, dtype=bool)
     while L > 1 and v[0] < L:
         left = 2 * v
         mL = mass(left)
-        mv = mass(v)
-        near |= np.abs(t - mL) <= tie_tol * np.abs(mv)
+        near |= np.abs(t - mL) <= tie_tol * np.abs(mroot)
         right_real = _node_first_row(tree, left + 1) < I
         go_right = (t >= mL) & right_real
         t = np.where(go_right, t - mL, t)
@@ -306,7 +306,7 @@ def _sts_walk(tree, U, Ggt, h, u, tie_tol):
     qs = np.sum(q, axis=1)
     tl = np.where(mleaf > 0, t * (qs / np.where(mleaf > 0, mleaf, 1.0)), 0.0)
     cq = np.cumsum(q, axis=1)
-    near |= np.any(np.abs(cq[:, :-1] - tl[:, None]) <= tie_tol * np.abs(qs)[:, None], axis=1)
+    near |= np.any(np.abs(cq[:, :-1] - tl[:, None]) <= tie_tol * np.abs(mroot)[:, None], axis=1)
     above = cq > tl[:, None]
     has = above.any(axis=1)
     first = np.argmax(above, axis=1)
@@ -324,8 +324,9 @@ def sts_draw(trees, factors, grams, n, J, seed, sweep, tie_tol=1e-12, batch=1024
     q_i = (U_k[i] (*) h)^T G_{>k} (U_k[i] (*) h); then h := h (*) U_k[i_k].
     Returns (idx (N, J), p (J,), near_tie (J,)) where p = h^T G^+ h / <G^+, G>_F
     is the exact leverage of the drawn row over the leverage total, and
-    near_tie marks draws with some decision within tie_tol * m(node) of its
-    threshold.  Draws are processed in batches of `batch` (they are independent).
+    near_tie marks draws with some decision within tie_tol * m(root) of its
+    threshold (the target t = u m(root) - sum of left masses carries rounding
+    on the scale of m(root), whatever the depth).  Draws are processed in batches of `batch` (they are independent).
     """
     N = len(factors)
     R = factors[0].shape[1]

@@ -249,6 +249,10 @@ cpd_status cpd_leverage_sample(cpd_handle h, int32_t mode, int64_t J, uint64_t s
                                double* out_prob) {
   if (!valid_mode(h, mode) || J < 1 || J > h->Jcap || !out_idx || !out_prob) return CPD_ERR_INVALID_ARG;
   if (h->opt.method == CPD_EXACT) return cpd_fail(h, CPD_ERR_INVALID_ARG, "handle built for exact ALS");
+  if (h->opt.method == CPD_STS_CP) {
+    cpd_status s = cpd_hadamard_pinv(h, mode, h->Gn, h->Gnpinv);
+    if (s != CPD_OK) return s;
+  }
   return cpd_draw(h, mode, J, nullptr, sweep, out_idx, out_prob, nullptr);
 }
 

@@ -67,8 +67,10 @@ struct cpd_ctx {
   // STS-CP state (Algorithm 4) per factor: heap of 2L node Grams
   int F = 0;
   int64_t L[CPD_MAX_MODES] = {0};
-  double* tree64[CPD_MAX_MODES] = {nullptr};  // 2L x R x R float64
-  float* tree32[CPD_MAX_MODES] = {nullptr};   // 2L x R x R float32 copy
+  float* tree32[CPD_MAX_MODES] = {nullptr};   // 2L x R(R+1)/2 float32 (upper triangles)
+  double* sts_ggt[CPD_MAX_MODES] = {nullptr}; // R x R: G^+ (*) Grams of factors drawn after k
+  double* sts_Z = nullptr;                    // <G^+, G>_F
+  float* sts_h = nullptr;                     // J x Rp running Hadamard products
 
   // per-update work buffers
   double* Gn = nullptr;        // R x R Hadamard of Grams for the solved mode

@@ -1,18 +1,358 @@
-// STS-CP sampler (Sec. 4.1, Appendix B, Algorithms 4-5).
+// STS-CP: draws from the exact leverage-score distribution of U_{!=n}
+// (Sec. 4.1 "STS-CP", Appendix B, Algorithms 4-5).
+//
+// Build (Algorithm 4 with one processor): per factor k a complete binary tree
+// in heap order; leaf l holds the Gram of rows [l F, (l+1) F) of U_k, every
+// internal node the sum of its children.  Matrices are stored as their upper
+// triangle (a <= b, row-major), float32.  Leaf count L is a power of two; the
+// leaves past the last row stay zero.
+//
+// Draw (Algorithm 5 with one processor): one warp per draw j.  For the factors
+// k != n in ascending order, with h the Hadamard product of the rows already
+// drawn (all ones at first) and G_{>k} = G^+ (*) Grams of the factors drawn
+// after k:
+//   m(v) = h^T (G^v (*) G_{>k}) h = sum_p c_p G^v_p M_p,  M_p = G_{>k,ab} h_a h_b
+// (c_p = 2 off the diagonal); the walk keeps the absolute target
+// t = u m(root) in float64, goes left iff t < m(left) and otherwise subtracts
+// m(left); at the leaf the row masses q_i = (U_k[i] (*) h)^T G_{>k} (U_k[i] (*) h)
+// are scanned (target rescaled by sum q / m(leaf)).  Masses are float32 sums;
+// the decisions therefore equal the float64 oracle's except within a float32
+// rounding distance of a threshold.  The draw probability is the exact
+// leverage of the drawn row over the leverage total,
+// p = h^T G^+ h / <G^+, G>_F.
 #include "common.cuh"
+#include <algorithm>
+#include <cstring>
 
-cpd_status cpd_sts_refresh(cpd_ctx* h, int mode) {
-  (void)mode;
-  return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP sampler not available in this build");
+namespace {
+
+constexpr int STS_NW = 4;   // warps per block
+
+__device__ __forceinline__ void pair_of(int p, int R, int& a, int& b) {
+  int aa = 0, rem = p;
+  while (rem >= R - aa) { rem -= R - aa; ++aa; }
+  a = aa;
+  b = aa + rem;
 }
 
-cpd_status cpd_sts_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep,
-                        unsigned long long sweep, int32_t* out_idx, double* out_p, double* out_w) {
-  (void)mode; (void)J; (void)d_sweep; (void)sweep; (void)out_idx; (void)out_p; (void)out_w;
-  return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP sampler not available in this build");
+// Leaf Grams: one block per leaf, the leaf's rows staged in shared memory.
+__global__ void sts_leaf_kernel(const float* __restrict__ U, int64_t I, int R, int Rp, int F, int64_t L,
+                                int64_t nleaf, float* __restrict__ tree) {
+  extern __shared__ float rows[];      // F x R
+  const int npairs = R * (R + 1) / 2;
+  for (int64_t l = blockIdx.x; l < nleaf; l += gridDim.x) {
+    const int64_t r0 = l * F;
+    const int nr = (int)(I - r0 < F ? I - r0 : F);
+    __syncthreads();
+    for (int e = threadIdx.x; e < F * R; e += blockDim.x) {
+      int i = e / R, c = e % R;
+      rows[e] = i < nr ? U[(r0 + i) * Rp + c] : 0.0f;
+    }
+    __syncthreads();
+    float* out = tree + (L + l) * npairs;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+      int a, b;
+      pair_of(p, R, a, b);
+      float s = 0.0f;
+      for (int i = 0; i < nr; ++i) s = fmaf(rows[i * R + a], rows[i * R + b], s);
+      out[p] = s;
+    }
+  }
 }
+
+// One level of the upward sums: nodes [lo, 2 lo).
+__global__ void sts_up_kernel(float* __restrict__ tree, int64_t lo, int npairs) {
+  const int64_t total = lo * npairs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = lo + e / npairs;
+    const int p = (int)(e % npairs);
+    tree[v * npairs + p] = tree[(2 * v) * npairs + p] + tree[(2 * v + 1) * npairs + p];
+  }
+}
+
+struct GgtArgs {
+  const double* G[CPD_MAX_MODES];
+  double* out[CPD_MAX_MODES];
+  int N, n, R;
+};
+
+// G_{>k} = G^+ (*) (*)_{k' > k, k' != n} G_{k'} for every k != n, and the
+// leverage total Z = <G^+, G>_F.
+__global__ void sts_ggt_kernel(GgtArgs a, const double* __restrict__ Gp, const double* __restrict__ Gh,
+                               double* __restrict__ Z) {
+  __shared__ double red[32];
+  const int RR = a.R * a.R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    for (int k = 0; k < a.N; ++k) {
+      if (k == a.n) continue;
+      double v = Gp[e];
+      for (int k2 = k + 1; k2 < a.N; ++k2)
+        if (k2 != a.n) v *= a.G[k2][e];
+      a.out[k][e] = v;
+    }
+  }
+  double s = 0.0;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) s += Gp[e] * Gh[e];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double z = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) z += red[w];
+    *Z = z;
+  }
+}
+
+struct StsArgs {
+  const float* tree;
+  const float* U;
+  const double* Ggt;
+  const double* Z;
+  float* Hs;
+  int32_t* out_idx;
+  double* out_p;
+  double* out_w;
+  const unsigned long long* d_sweep;
+  unsigned long long h_sweep, seed;
+  int64_t I, L, J;
+  int R, Rp, F, D, npairs, k, n, N, first, last;
+};
+
+template <int RB>
+__global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
+  extern __shared__ float4 sm4[];
+  float* Gs = reinterpret_cast<float*>(sm4);                      // R x R
+  const int R = a.R, Rp = a.Rp, npairs = a.npairs;
+  const int npad = (npairs + 3) & ~3;
+  unsigned char* pa = reinterpret_cast<unsigned char*>(Gs + R * R);
+  unsigned char* pb = pa + npad;
+  float* wbase = reinterpret_cast<float*>(pb + npad);
+  const int per_warp = npad + Rp + ((a.F + 3) & ~3);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* M = wbase + wid * per_warp;
+  float* hs = M + npad;
+  float* qb = hs + Rp;
+
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Gs[e] = (float)a.Ggt[e];
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    int x, y;
+    pair_of(p, R, x, y);
+    pa[p] = (unsigned char)x;
+    pb[p] = (unsigned char)y;
+  }
+  __syncthreads();
+  const unsigned long long s = a.d_sweep ? *a.d_sweep : a.h_sweep;
+  const double Z = *a.Z;
+  const int64_t warp = (int64_t)blockIdx.x * STS_NW + wid;
+  const int64_t nwarps = (int64_t)gridDim.x * STS_NW;
+
+  auto mass = [&](int64_t v) -> float {
+    const float* g = a.tree + v * npairs;
+    float acc = 0.0f;
+    for (int p = lane; p < npairs; p += 32) acc = fmaf(g[p], M[p], acc);
+    return warp_sum(acc);
+  };
+
+  for (int64_t j = warp; j < a.J; j += nwarps) {
+    for (int r = lane; r < Rp; r += 32) hs[r] = a.first ? (r < R ? 1.0f : 0.0f) : a.Hs[j * Rp + r];
+    __syncwarp();
+    for (int p = lane; p < npairs; p += 32) {
+      const int x = pa[p], y = pb[p];
+      M[p] = (x == y ? 1.0f : 2.0f) * Gs[x * R + y] * hs[x] * hs[y];
+    }
+    __syncwarp();
+    const double u = cpd_uniform(a.seed, CPD_STREAM_STS, (unsigned long long)j, (unsigned long long)a.k,
+                                 (unsigned long long)a.n, s);
+    double t = u * (double)mass(1);
+    int64_t v = 1;
+    int depth = 0;
+    while (v < a.L) {
+      const int64_t left = 2 * v;
+      const float mL = mass(left);
+      const int64_t rfirst = (((left + 1) << (a.D - depth - 1)) - a.L) * a.F;
+      if (t >= (double)mL && rfirst < a.I) { t -= (double)mL; v = left + 1; }
+      else v = left;
+      ++depth;
+    }
+    const int64_t r0 = (v - a.L) * a.F;
+    const int nr = (int)(a.I - r0 < a.F ? a.I - r0 : a.F);
+    const float mleaf = mass(v);
+    // row masses of the leaf
+    double qpart = 0.0;
+    for (int c0 = 0; c0 < nr; c0 += 32) {
+      const int i = c0 + lane;
+      float q = 0.0f;
+      if (i < nr) {
+        const float* urow = a.U + (r0 + i) * Rp;
+        float x[RB];
+#pragma unroll
+        for (int c = 0; c < RB; ++c) x[c] = (c < R) ? urow[c] * hs[c] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < RB; ++c) {
+          if (c < R) {
+            float y = 0.0f;
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+              if (b < R) y = fmaf(Gs[c * R + b], x[b], y);
+            q = fmaf(x[c], y, q);
+          }
+        }
+        qb[i] = q;
+      }
+      qpart += (double)q;
+    }
+    __syncwarp();
+    const double qs = warp_sum(qpart);
+    const double tl = mleaf > 0.0f ? t * (qs / (double)mleaf) : 0.0;
+    int found = -1;
+    double carry = 0.0;
+    for (int c0 = 0; c0 < nr && found < 0; c0 += 32) {
+      const int i = c0 + lane;
+      const double qd = i < nr ? (double)qb[i] : 0.0;
+      double cum = qd;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        double y = __shfl_up_sync(CPD_FULL, cum, o);
+        if (lane >= o) cum += y;
+      }
+      cum += carry;
+      const unsigned hit = __ballot_sync(CPD_FULL, i < nr && cum > tl);
+      if (hit) found = c0 + __ffs(hit) - 1;
+      carry = __shfl_sync(CPD_FULL, cum, 31);
+    }
+    if (found < 0) {              // rounding put the target past the end
+      found = 0;
+      for (int c0 = 0; c0 < nr; c0 += 32) {
+        const int i = c0 + lane;
+        const unsigned pos = __ballot_sync(CPD_FULL, i < nr && qb[i] > 0.0f);
+        if (pos) found = c0 + 31 - __clz(pos);
+      }
+    }
+    const int64_t ik = r0 + found;
+    if (lane == 0) {
+      a.out_idx[(int64_t)a.k * a.J + j] = (int32_t)ik;
+      if (a.first) a.out_idx[(int64_t)a.n * a.J + j] = -1;
+    }
+    __syncwarp();
+    for (int r = lane; r < Rp; r += 32) {
+      const float hn = (r < R) ? hs[r] * a.U[ik * Rp + r] : 0.0f;
+      hs[r] = hn;
+      if (!a.last) a.Hs[j * Rp + r] = hn;
+    }
+    __syncwarp();
+    if (a.last) {
+      // G_{>k} of the last factor is G^+: leverage of the drawn KRP row
+      float acc = 0.0f;
+      for (int p = lane; p < npairs; p += 32) {
+        const int x = pa[p], y = pb[p];
+        acc = fmaf((x == y ? 1.0f : 2.0f) * Gs[x * R + y], hs[x] * hs[y], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const double prob = (double)acc / Z;
+        if (a.out_p) a.out_p[j] = prob;
+        if (a.out_w) a.out_w[j] = 1.0 / ((double)a.J * prob);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+size_t sts_smem(int R, int F) {
+  const int npairs = R * (R + 1) / 2;
+  const int npad = (npairs + 3) & ~3;
+  const int Rp = cpd_pad4(R);
+  const int per_warp = npad + Rp + ((F + 3) & ~3);
+  return (size_t)R * R * 4 + 2 * (size_t)npad + (size_t)STS_NW * per_warp * 4;
+}
+
+template <int RB>
+cpd_status launch_draw(cpd_ctx* h, const StsArgs& a) {
+  const size_t shm = sts_smem(h->R, h->F);
+  const int64_t blocks = std::min<int64_t>(cpd_ceil_div(a.J, STS_NW), (int64_t)h->num_sms * 16);
+  sts_draw_kernel<RB><<<(unsigned)blocks, STS_NW * 32, shm, h->stream>>>(a);
+  CPD_LAUNCH(h, "sts_draw");
+  return CPD_OK;
+}
+
+}  // namespace
 
 cpd_status cpd_sts_alloc(cpd_ctx* h) {
-  (void)h;
+  const int R = h->R;
+  const int npairs = R * (R + 1) / 2;
+  if (h->F < 1 || (int64_t)h->F * R > 16384 || h->F > 1024)
+    return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP leaf_rows must satisfy 1 <= F and F * R <= 16384");
+  if (sts_smem(R, h->F) > 227 * 1024) return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP tile exceeds shared memory");
+  cpd_status s;
+  for (int k = 0; k < h->N; ++k) {
+    const int64_t nleaf = cpd_ceil_div(h->dims[k], h->F);
+    int64_t L = 1;
+    while (L < nleaf) L <<= 1;
+    h->L[k] = L;
+    if ((s = cpd_alloc(h, &h->tree32[k], (size_t)(2 * L) * npairs)) != CPD_OK) return s;
+    CPD_CUDA(h, cudaMemsetAsync(h->tree32[k], 0, (size_t)(2 * L) * npairs * sizeof(float), h->stream));
+    if ((s = cpd_alloc(h, &h->sts_ggt[k], (size_t)R * R)) != CPD_OK) return s;
+  }
+  if ((s = cpd_alloc(h, &h->sts_Z, 1)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->sts_h, (size_t)std::max<int64_t>(h->opt.samples, 1) * h->Rp)) != CPD_OK) return s;
+  const int shm = (int)sts_smem(R, h->F);
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  const int lshm = h->F * R * 4;
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lshm));
+  return CPD_OK;
+}
+
+// Algorithm 4 with one processor: leaf Grams, then the levels upward.
+cpd_status cpd_sts_refresh(cpd_ctx* h, int k) {
+  PhaseTimer pt(h, CPD_PHASE_SAMPLER);
+  const int R = h->R, npairs = R * (R + 1) / 2;
+  const int64_t I = h->dims[k], L = h->L[k];
+  const int64_t nleaf = cpd_ceil_div(I, h->F);
+  const int grid = (int)std::min<int64_t>(nleaf, (int64_t)h->num_sms * 8);
+  sts_leaf_kernel<<<grid, 256, (size_t)h->F * R * 4, h->stream>>>(h->U[k], I, R, h->Rp, h->F, L, nleaf, h->tree32[k]);
+  CPD_LAUNCH(h, "sts_leaf");
+  for (int64_t lo = L / 2; lo >= 1; lo /= 2) {
+    const int64_t total = lo * npairs;
+    const int g = (int)std::min<int64_t>(cpd_ceil_div(total, 256), (int64_t)h->num_sms * 8);
+    sts_up_kernel<<<g, 256, 0, h->stream>>>(h->tree32[k], lo, npairs);
+    CPD_LAUNCH(h, "sts_up");
+  }
+  return CPD_OK;
+}
+
+// Requires h->Gn / h->Gnpinv of `mode` (cpd_hadamard_pinv) on the stream.
+cpd_status cpd_sts_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep, unsigned long long sweep,
+                        int32_t* out_idx, double* out_p, double* out_w) {
+  if (J <= 0) return CPD_OK;
+  PhaseTimer pt(h, CPD_PHASE_DRAW);
+  GgtArgs g;
+  memset(&g, 0, sizeof(g));
+  for (int k = 0; k < h->N; ++k) { g.G[k] = h->G[k]; g.out[k] = h->sts_ggt[k]; }
+  g.N = h->N; g.n = mode; g.R = h->R;
+  sts_ggt_kernel<<<1, 256, 0, h->stream>>>(g, h->Gnpinv, h->Gn, h->sts_Z);
+  CPD_LAUNCH(h, "sts_ggt");
+  int firstk = -1, lastk = -1;
+  for (int k = 0; k < h->N; ++k)
+    if (k != mode) { if (firstk < 0) firstk = k; lastk = k; }
+  for (int k = 0; k < h->N; ++k) {
+    if (k == mode) continue;
+    StsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tree = h->tree32[k]; a.U = h->U[k]; a.Ggt = h->sts_ggt[k]; a.Z = h->sts_Z; a.Hs = h->sts_h;
+    a.out_idx = out_idx; a.out_p = out_p; a.out_w = out_w;
+    a.d_sweep = d_sweep; a.h_sweep = sweep; a.seed = h->opt.seed;
+    a.I = h->dims[k]; a.L = h->L[k]; a.J = J;
+    a.R = h->R; a.Rp = h->Rp; a.F = h->F; a.npairs = h->R * (h->R + 1) / 2;
+    int D = 0;
+    while ((1ll << D) < a.L) ++D;
+    a.D = D; a.k = k; a.n = mode; a.N = h->N; a.first = (k == firstk); a.last = (k == lastk);
+    cpd_status s;
+    if (h->R <= 32) s = launch_draw<32>(h, a);
+    else if (h->R <= 64) s = launch_draw<64>(h, a);
+    else s = launch_draw<128>(h, a);
+    if (s != CPD_OK) return s;
+  }
   return CPD_OK;
 }
