@@ -212,12 +212,14 @@ def ours(args, world, rank, local):
     clk.start()
     barrier(world)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
         cpd.cpd_als_sweep(h, 1, sync=False)
         stops[i].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier(world)
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]

@@ -181,6 +181,36 @@ __device__ __forceinline__ double cpd_uniform(unsigned long long seed, unsigned 
   return (double)(c[0] >> 11) * 0x1.0p-53;
 }
 
+// ---- double-float ("df64") accumulation on the float32 pipes ---------------
+// GB300 issues float64 FMAs at 1/64 of the float32 rate, so the float64-exact
+// Grams and leverage scores are accumulated as unevaluated sums hi + lo of two
+// float32 with error-free transformations: Knuth's TwoSum and the FMA-based
+// TwoProduct (Dekker; Ogita, Rump, Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 2005).  The intrinsics keep the compiler from
+// contracting or reassociating them.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += x * y exactly up to the float32 rounding of lo.
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float pe = __fmaf_rn(x, y, -p);
+  float s, e;
+  df_two_sum(hi, p, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+// (hi, lo) += v for a float32 v
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+  float s, e;
+  df_two_sum(hi, v, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+__device__ __forceinline__ double df_value(float hi, float lo) { return (double)hi + (double)lo; }
+
 #define CPD_STREAM_ARLS 0ull
 #define CPD_STREAM_STS 1ull
 

@@ -56,11 +56,13 @@ __global__ void sigma_kernel(const double* __restrict__ part, int nblk, int R, d
 }
 
 // U_out = U_in / sigma (columns with sigma = 0 kept), padded columns zeroed,
-// and float64 Gram partials of the stored float32 values.
+// and float64 Gram partials of the stored float32 values.  Per 64-row tile a
+// thread accumulates its Gram entries as df64 sums of exact float32 products
+// (error ~ 64 * 2^-48 of the sum of |terms|), then adds them into float64.
 __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart) {
-  extern __shared__ double tile[];                     // TR x R float64
+  extern __shared__ float tile[];                      // TR x R float32
   __shared__ float inv[CPD_MAX_RANK];
   __shared__ unsigned char pa[8320], pb[8320];
   const int t = threadIdx.x;
@@ -90,9 +92,9 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
         float v = 0.0f;
         if (c < R) v = Uin[i * Rp + c] * inv[c];
         Uout[i * Rp + c] = v;
-        if (c < R) tile[rr * R + c] = (double)v;
+        if (c < R) tile[rr * R + c] = v;
       } else if (c < R) {
-        tile[rr * R + c] = 0.0;
+        tile[rr * R + c] = 0.0f;
       }
     }
     __syncthreads();
@@ -100,10 +102,11 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     for (int m = 0; m < MAXP; ++m) {
       int p = t + m * DTHREADS;
       if (p < npairs) {
-        int a = pa[p], b = pb[p];
-        double s = acc[m];
-        for (int rr = 0; rr < TR; ++rr) s = fma(tile[rr * R + a], tile[rr * R + b], s);
-        acc[m] = s;
+        const int a = pa[p], b = pb[p];
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll 8
+        for (int rr = 0; rr < TR; ++rr) df_fma(hi, lo, tile[rr * R + a], tile[rr * R + b]);
+        acc[m] += df_value(hi, lo);
       }
     }
     __syncthreads();
@@ -440,7 +443,7 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
                             double* G) {
   const int R = h->R;
   PhaseTimer pt(h, CPD_PHASE_GRAM);
-  size_t shm = (size_t)TR * R * sizeof(double);
+  size_t shm = (size_t)TR * R * sizeof(float);
   normalize_gram_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
                                                                       h->Gpart);
   CPD_LAUNCH(h, "normalize_gram");
@@ -540,7 +543,7 @@ cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out) {
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in.
 cpd_status cpd_dense_init(cpd_ctx* h) {
   const int R = h->R;
-  size_t s1 = (size_t)TR * R * sizeof(double);
+  size_t s1 = (size_t)TR * R * sizeof(float);
   size_t s2 = (size_t)R * R * sizeof(double);
   size_t s3 = (size_t)(2 * R * R + TR * R) * sizeof(float);
   CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));

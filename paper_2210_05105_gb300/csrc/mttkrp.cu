@@ -149,6 +149,10 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
   const uint32_t nu = min(a.counters[0], a.uq_cap);
   const uint32_t total = a.counters[1];
   const int64_t nchunks = ((int64_t)total + 31) / 32;
+  const int C = a.Rp / 4;                 // float4 chunks per row
+  const int E = C >= 32 ? 1 : 32 / C;     // nonzeros per warp instruction
+  const int sub = C >= 32 ? 0 : lane / C; // which of the E nonzeros this lane serves
+  const int q = C >= 32 ? lane : lane % C;
   for (int64_t c = warp; c < nchunks; c += nwarps) {
     const int64_t p = c * 32 + lane;
     uint32_t row = 0, useg = 0;
@@ -167,13 +171,23 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
       scale = (float)(a.dd_w[slot] * (double)__uint_as_float(en.y));
     }
     const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
-    for (int j = 0; j < cnt; ++j) {
-      const uint32_t rj = __shfl_sync(CPD_FULL, row, j);
-      const float sj = __shfl_sync(CPD_FULL, scale, j);
-      const uint32_t uj = __shfl_sync(CPD_FULL, useg, j);
-      const float* hrow = a.H + (int64_t)uj * a.Rp;
-      float* yrow = Y + (int64_t)rj * a.Rp;
-      for (int r = lane; r < a.R; r += 32) atomicAdd(yrow + r, sj * hrow[r]);
+    // C lanes cover one row of Rp floats with 16-byte vector reductions, so
+    // one warp instruction updates E = 32 / C selected nonzeros at once.
+    for (int j0 = 0; j0 < cnt; j0 += E) {
+      const int jj = j0 + sub;
+      const int src = jj < 32 ? jj : 31;
+      const uint32_t rj = __shfl_sync(CPD_FULL, row, src);
+      const float sj = __shfl_sync(CPD_FULL, scale, src);
+      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
+      if (sub < E && jj < cnt) {
+        for (int qq = q; qq < C; qq += 32) {
+          const float4 hv = reinterpret_cast<const float4*>(a.H + (int64_t)uj * a.Rp)[qq];
+          float* yp = Y + (int64_t)rj * a.Rp + 4 * qq;
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj * hv.x), "f"(sj * hv.y),
+                       "f"(sj * hv.z), "f"(sj * hv.w)
+                       : "memory");
+        }
+      }
     }
   }
 }

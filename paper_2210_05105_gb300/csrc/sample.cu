@@ -16,17 +16,26 @@ namespace {
 constexpr int LEV_THREADS = 256;
 
 // ell_i = || B u_i ||^2 with G_k^+ = B^T B (B lower triangular when G_k was
-// factored by Cholesky).  One row per thread; u_i in registers, B in shared
-// memory (every thread reads the same entry: broadcast).  Also writes the sum
-// of each block's 256 scores.
+// factored by Cholesky).  One row per thread; u_i in registers, B split into
+// float32 hi + lo in shared memory (every thread reads the same entry:
+// broadcast).  y = B u and ||y||^2 are accumulated in df64 on the float32
+// pipes (error-free products, TwoSum), i.e. to ~2^-48 relative instead of
+// float64 FMAs at 1/64 rate.  Also writes the sum of each block's scores.
 template <int RB>
 __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
                                                           const double* __restrict__ B, const int* __restrict__ tri,
                                                           double* __restrict__ ell, double* __restrict__ blk) {
-  extern __shared__ double Bs[];     // R x R
+  extern __shared__ float Bsm[];     // hi: R x R, lo: R x R
   __shared__ double red[LEV_THREADS / 32];
+  float* Bhi = Bsm;
+  float* Blo = Bsm + R * R;
   const int t = threadIdx.x;
-  for (int e = t; e < R * R; e += LEV_THREADS) Bs[e] = B[e];
+  for (int e = t; e < R * R; e += LEV_THREADS) {
+    const double b = B[e];
+    const float hi = (float)b;
+    Bhi[e] = hi;
+    Blo[e] = (float)(b - (double)hi);
+  }
   const bool lower = *tri != 0;
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * LEV_THREADS + t;
@@ -43,26 +52,37 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
         u[4 * q] = u[4 * q + 1] = u[4 * q + 2] = u[4 * q + 3] = 0.0f;
       }
     }
+    float lh = 0.0f, ll = 0.0f;
     if (lower) {
 #pragma unroll
       for (int a = 0; a < RB; ++a) {
         if (a < R) {
-          double y = 0.0;
+          float yh = 0.0f, yl = 0.0f;
 #pragma unroll
-          for (int b = 0; b <= a; ++b) y = fma(Bs[a * R + b], (double)u[b], y);
-          l = fma(y, y, l);
+          for (int b = 0; b <= a; ++b) {
+            df_fma(yh, yl, Bhi[a * R + b], u[b]);
+            yl = __fmaf_rn(Blo[a * R + b], u[b], yl);
+          }
+          df_fma(lh, ll, yh, yh);
+          ll = __fmaf_rn(__fmul_rn(2.0f, yh), yl, ll);
         }
       }
     } else {
 #pragma unroll 1
       for (int a = 0; a < R; ++a) {
-        double y = 0.0;
+        float yh = 0.0f, yl = 0.0f;
 #pragma unroll
-        for (int b = 0; b < RB; ++b)
-          if (b < R) y = fma(Bs[a * R + b], (double)u[b], y);
-        l = fma(y, y, l);
+        for (int b = 0; b < RB; ++b) {
+          if (b < R) {
+            df_fma(yh, yl, Bhi[a * R + b], u[b]);
+            yl = __fmaf_rn(Blo[a * R + b], u[b], yl);
+          }
+        }
+        df_fma(lh, ll, yh, yh);
+        ll = __fmaf_rn(__fmul_rn(2.0f, yh), yl, ll);
       }
     }
+    l = df_value(lh, ll);
     ell[i] = l;
   }
   // block sum in a fixed order
@@ -161,7 +181,7 @@ cpd_status launch_lev(cpd_ctx* h, int k) {
   PhaseTimer pt(h, CPD_PHASE_SAMPLER);
   const int64_t I = h->dims[k];
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
-  size_t shm = (size_t)h->R * h->R * sizeof(double);
+  size_t shm = (size_t)h->R * h->R * 2 * sizeof(float);
   lev_kernel<RB><<<(unsigned)nb, LEV_THREADS, shm, h->stream>>>(h->U[k], I, h->R, h->Rp, h->Bk[k], h->Btri + k,
                                                                  h->ell[k], h->blk[k]);
   CPD_LAUNCH(h, "lev");

@@ -2,8 +2,9 @@
 
 The GPU sums the tree masses in float32; a draw may therefore differ from
 the oracle only where the oracle finds a decision within 1e-5 * m(root) of
-its threshold (the oracle's near-tie flag at that tolerance).  Probabilities
-of equal draws agree to 1e-5 relative; fits to 1e-3.
+its threshold (the oracle's near-tie flag at that tolerance), and at most 1%
+of the draws may differ at these sizes.  Probabilities of equal draws agree
+to 1e-5 relative; fits to 1e-3.
 """
 import numpy as np
 import pytest
@@ -44,7 +45,7 @@ def test_sts_draws_match_oracle(cpd, dims, R, F, nnz):
         gi = gi.cpu().numpy()
         mism = np.any(gi != oi, axis=0)
         assert not np.any(mism & ~near), "STS draw differs away from a near-tie"
-        assert near.mean() < 0.02
+        assert mism.mean() < 0.01
         ok = ~mism
         assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-5
         assert np.all(gi[mode] == -1)
