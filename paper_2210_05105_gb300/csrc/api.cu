@@ -165,10 +165,8 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_alloc(h, &h->H, (size_t)h->Jcap * Rp)) != CPD_OK) return s;
 
   if (h->opt.method == CPD_ARLS_LEV) {
-    if ((s = cpd_alloc(h, &h->Btri, (size_t)N)) != CPD_OK) return s;
     for (int k = 0; k < N; ++k) {
       if ((s = cpd_alloc(h, &h->Gkpinv[k], (size_t)R * R)) != CPD_OK) return s;
-      if ((s = cpd_alloc(h, &h->Bk[k], (size_t)R * R)) != CPD_OK) return s;
       if ((s = cpd_alloc(h, &h->ell[k], (size_t)dims[k])) != CPD_OK) return s;
       if ((s = cpd_alloc(h, &h->cdf[k], (size_t)dims[k])) != CPD_OK) return s;
       if ((s = cpd_alloc(h, &h->blk[k], (size_t)cpd_ceil_div(dims[k], 256))) != CPD_OK) return s;

@@ -58,8 +58,6 @@ struct cpd_ctx {
 
   // CP-ARLS-LEV state (Algorithm 2) per factor
   double* Gkpinv[CPD_MAX_MODES] = {nullptr};  // R x R
-  double* Bk[CPD_MAX_MODES] = {nullptr};      // R x R, G_k^+ = B^T B
-  int* Btri = nullptr;                        // N flags: B lower triangular
   double* ell[CPD_MAX_MODES] = {nullptr};     // I_k
   double* cdf[CPD_MAX_MODES] = {nullptr};     // I_k inclusive running sums
   double* blk[CPD_MAX_MODES] = {nullptr};     // per-block partial sums of ell
@@ -221,7 +219,7 @@ cpd_status cpd_build_layouts(cpd_ctx* h);
 cpd_status cpd_renormalize_inputs(cpd_ctx* h);
 cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G);
 cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout);
-cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P, double* B, int* tri);
+cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P);
 cpd_status cpd_dense_init(cpd_ctx* h);
 cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_sigma);
 cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out);

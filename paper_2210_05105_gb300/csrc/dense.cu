@@ -45,13 +45,14 @@ __global__ void colsq_kernel(const float* __restrict__ U, int64_t I, int R, int 
   store_col_partials(g < groups ? acc : 0.0, R, groups, part + (int64_t)blockIdx.x * R);
 }
 
-// sigma_r = sqrt(sum of partials), fixed order.
+// sigma_r = sqrt(sum of partials): one warp per column, fixed order.
 __global__ void sigma_kernel(const double* __restrict__ part, int nblk, int R, double* __restrict__ sigma) {
-  int r = threadIdx.x;
-  if (r < R) {
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * R + r];
-    sigma[r] = sqrt(s);
+    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * R + r];
+    s = warp_sum(s);
+    if (lane == 0) sigma[r] = sqrt(s);
   }
 }
 
@@ -119,17 +120,23 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
   }
 }
 
-// G = sum of block partials in fixed order; full symmetric R x R.
+// G = sum of block partials, one warp per Gram entry: lane l sums the
+// partials l, l+32, ... in order, then a fixed butterfly (deterministic).
 __global__ void gram_reduce_kernel(const double* __restrict__ gpart, int nblk, int R, double* __restrict__ G) {
   const int npairs = R * (R + 1) / 2;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < npairs; p += nw) {
     int a = 0, rem = p;
     while (rem >= R - a) { rem -= R - a; ++a; }
-    int b = a + rem;
+    const int b = a + rem;
     double s = 0.0;
-    for (int k = 0; k < nblk; ++k) s += gpart[(int64_t)k * npairs + p];
-    G[a * R + b] = s;
-    G[b * R + a] = s;
+    for (int k = lane; k < nblk; k += 32) s += gpart[(int64_t)k * npairs + p];
+    s = warp_sum(s);
+    if (lane == 0) {
+      G[a * R + b] = s;
+      G[b * R + a] = s;
+    }
   }
 }
 
@@ -139,8 +146,6 @@ struct PinvJob {
   int nin;
   double* out_had;                  // may be null
   double* out_pinv;
-  double* out_factor;               // may be null: B with G^+ = B^T B
-  int* out_tri;                     // may be null: 1 if B is lower triangular
   double* scratch;                  // 2 R x R float64 (global)
 };
 struct PinvJobs { PinvJob job[2]; };
@@ -162,15 +167,18 @@ __device__ double block_sum_d(double v, double* red) {
   return r;
 }
 
-// Cholesky G = L L^T and G^{-1} = L^{-T} L^{-1} when every pivot exceeds
-// 1e-9 * max diag; otherwise a parallel (round-robin) cyclic Jacobi
-// eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped.
+// Inverse of a symmetric positive definite G by Gauss-Jordan elimination
+// without pivoting (the pivots are the Cholesky / LDL^T pivots) when every
+// pivot exceeds 1e-9 * max diag; otherwise a parallel (round-robin) cyclic
+// Jacobi eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped.
+// One block; each elimination step copies row and column k aside, then every
+// thread updates its entries (two barriers per step, no serial thread).
 __global__ void __launch_bounds__(DTHREADS) pinv_kernel(PinvJobs jobs, int R) {
   extern __shared__ double A[];                     // R x R
   __shared__ double red[40];
-  __shared__ int flag;
   __shared__ int sp[64], sq[64];
   __shared__ double sc[64], ss[64];
+  __shared__ double rowk[CPD_MAX_RANK], colk[CPD_MAX_RANK];
   const PinvJob& jb = jobs.job[blockIdx.x];
   const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
@@ -180,52 +188,32 @@ __global__ void __launch_bounds__(DTHREADS) pinv_kernel(PinvJobs jobs, int R) {
     A[e] = v;
     if (jb.out_had) jb.out_had[e] = v;
   }
-  if (t == 0) flag = 0;
   __syncthreads();
   double maxdiag = 0.0;
   for (int a = 0; a < R; ++a) maxdiag = fmax(maxdiag, fabs(A[a * R + a]));
-  // -- Cholesky, lower triangle in place
+  bool singular = false;
   for (int k = 0; k < R; ++k) {
-    if (t == 0) {
-      double d = A[k * R + k];
-      if (!(d > 1e-9 * maxdiag) || !isfinite(d)) flag = 1;
-      else A[k * R + k] = sqrt(d);
-    }
+    if (t < R) { rowk[t] = A[k * R + t]; colk[t] = A[t * R + k]; }
     __syncthreads();
-    if (flag) break;
-    const double lkk = A[k * R + k];
-    for (int i = k + 1 + t; i < R; i += nt) A[i * R + k] /= lkk;
-    __syncthreads();
-    const int m = R - k - 1;
-    for (int e = t; e < m * m; e += nt) {
-      int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) A[i * R + j] -= A[i * R + k] * A[j * R + k];
+    const double piv = rowk[k];
+    if (!(piv > 1e-9 * maxdiag) || !isfinite(piv)) { singular = true; break; }   // uniform
+    const double inv = 1.0 / piv;
+    for (int e = t; e < RR; e += nt) {
+      const int i = e / R, j = e % R;
+      double v;
+      if (i == k) v = (j == k) ? inv : rowk[j] * inv;
+      else if (j == k) v = -colk[i] * inv;
+      else v = A[e] - colk[i] * (rowk[j] * inv);
+      A[e] = v;
     }
     __syncthreads();
   }
-  double* W = jb.scratch;             // R x R
   double* V = jb.scratch + RR;        // R x R
-  if (!flag) {
-    // W = L^{-1}, one column per thread
-    for (int j = t; j < R; j += nt) {
-      for (int i = 0; i < j; ++i) W[i * R + j] = 0.0;
-      W[j * R + j] = 1.0 / A[j * R + j];
-      for (int i = j + 1; i < R; ++i) {
-        double s = 0.0;
-        for (int m = j; m < i; ++m) s = fma(A[i * R + m], W[m * R + j], s);
-        W[i * R + j] = -s / A[i * R + i];
-      }
-    }
-    __syncthreads();
+  if (!singular) {
     for (int e = t; e < RR; e += nt) {
-      int a = e / R, b = e % R;
-      int m0 = a > b ? a : b;
-      double s = 0.0;
-      for (int m = m0; m < R; ++m) s = fma(W[m * R + a], W[m * R + b], s);
-      jb.out_pinv[e] = s;
-      if (jb.out_factor) jb.out_factor[e] = W[e];
+      const int i = e / R, j = e % R;
+      jb.out_pinv[e] = 0.5 * (A[e] + A[j * R + i]);
     }
-    if (t == 0 && jb.out_tri) *jb.out_tri = 1;
     return;
   }
   // -- Jacobi fallback: reload A, V = I
@@ -309,60 +297,78 @@ __global__ void __launch_bounds__(DTHREADS) pinv_kernel(PinvJobs jobs, int R) {
       if (lam > cut) s += V[a * R + m] * (V[b * R + m] / lam);
     }
     jb.out_pinv[e] = s;
-    if (jb.out_factor) {   // row m of B: sqrt(1 / lambda_m) v_m^T
-      double lam = A[a * R + a];
-      jb.out_factor[e] = (lam > cut) ? V[b * R + a] / sqrt(lam) : 0.0;
-    }
   }
-  if (t == 0 && jb.out_tri) *jb.out_tri = 0;
 }
 
 // ---- solve: Uw = Y (P_hi + P_lo), float32 with the float64 G^+ split ----
+// One row per thread, the row of Y in registers, P in shared memory (all
+// threads read the same entry: broadcast); outputs in chunks of 32 columns
+// written as 16-byte vectors.  Column sums of squares: warp sums per row
+// batch into shared memory, then a fixed-order sum per block.
+template <int RB>
 __global__ void __launch_bounds__(DTHREADS) solve_kernel(
     const float* __restrict__ Y, const double* __restrict__ P, float* __restrict__ Uw, int64_t I, int R,
     int Rp, double* __restrict__ colpart) {
   extern __shared__ float sm[];
   float* Phi = sm;                 // R x R
   float* Plo = sm + R * R;         // R x R
-  float* Yt = sm + 2 * R * R;      // TR x R
-  const int t = threadIdx.x;
+  __shared__ double wsq[DTHREADS / 32][CPD_MAX_RANK];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   for (int e = t; e < R * R; e += DTHREADS) {
-    double p = P[e];
-    float hi = (float)p;
+    const double p = P[e];
+    const float hi = (float)p;
     Phi[e] = hi;
     Plo[e] = (float)(p - (double)hi);
   }
-  const int groups = DTHREADS / R;
-  const int c = t % R, g = t / R;
-  double acc = 0.0;
-  const int64_t ntiles = cpd_ceil_div(I, TR);
+  for (int c = lane; c < CPD_MAX_RANK; c += 32) wsq[wid][c] = 0.0;
   __syncthreads();
-  for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
-    const int64_t r0 = tl * TR;
-    for (int e = t; e < TR * R; e += DTHREADS) {
-      int rr = e / R, cc = e % R;
-      int64_t i = r0 + rr;
-      Yt[e] = (i < I) ? Y[i * Rp + cc] : 0.0f;
+  for (int64_t r0 = (int64_t)blockIdx.x * DTHREADS; r0 < I; r0 += (int64_t)gridDim.x * DTHREADS) {
+    const int64_t i = r0 + t;
+    const bool live = i < I;
+    float y[RB];
+    const float4* yrow = reinterpret_cast<const float4*>(Y + (live ? i : 0) * Rp);
+#pragma unroll
+    for (int q = 0; q < RB / 4; ++q) {
+      float4 v = (live && 4 * q < Rp) ? yrow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
     }
-    __syncthreads();
-    if (g < groups) {
-      for (int rr = g; rr < TR; rr += groups) {
-        int64_t i = r0 + rr;
-        if (i >= I) break;
-        float sh = 0.0f, sl = 0.0f;
-        for (int a = 0; a < R; ++a) {
-          float y = Yt[rr * R + a];
-          sh = fmaf(y, Phi[a * R + c], sh);
-          sl = fmaf(y, Plo[a * R + c], sl);
+    for (int c0 = 0; c0 < Rp; c0 += 32) {
+      float out[32];
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) out[cc] = 0.0f;
+#pragma unroll
+      for (int a = 0; a < RB; ++a) {
+        if (a < R) {
+          const float ya = y[a];
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) {
+            const int c = c0 + cc;
+            if (c < R) out[cc] = fmaf(ya, Phi[a * R + c], fmaf(ya, Plo[a * R + c], out[cc]));
+          }
         }
-        float v = sh + sl;
-        Uw[i * Rp + c] = v;
-        acc += (double)(v * v);
+      }
+      if (live) {
+        float4* urow = reinterpret_cast<float4*>(Uw + i * Rp + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (c0 + 4 * q < Rp) urow[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+      }
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) {
+        const int c = c0 + cc;
+        if (c < R) {
+          double sq = warp_sum((double)(out[cc] * out[cc]));
+          if (lane == 0) wsq[wid][c] += sq;
+        }
       }
     }
-    __syncthreads();
   }
-  store_col_partials(g < groups ? acc : 0.0, R, groups, colpart + (int64_t)blockIdx.x * R);
+  __syncthreads();
+  for (int c = t; c < R; c += DTHREADS) {
+    double s = 0.0;
+    for (int w = 0; w < DTHREADS / 32; ++w) s += wsq[w][c];
+    colpart[(int64_t)blockIdx.x * R + c] = s;
+  }
 }
 
 // ---- fit ------------------------------------------------------------------
@@ -447,7 +453,7 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
   normalize_gram_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
                                                                       h->Gpart);
   CPD_LAUNCH(h, "normalize_gram");
-  gram_reduce_kernel<<<std::max(1, (R * (R + 1) / 2 + 255) / 256), 256, 0, h->stream>>>(h->Gpart, h->gram_blocks, R, G);
+  gram_reduce_kernel<<<std::max(1, (R * (R + 1) / 2 + 7) / 8), 256, 0, h->stream>>>(h->Gpart, h->gram_blocks, R, G);
   CPD_LAUNCH(h, "gram_reduce");
   return CPD_OK;
 }
@@ -461,7 +467,7 @@ cpd_status cpd_renormalize_inputs(cpd_ctx* h) {
   const int R = h->R;
   for (int k = 0; k < h->N; ++k) {
     colsq_kernel<<<h->gram_blocks, DTHREADS, 0, h->stream>>>(h->U[k], h->dims[k], R, h->Rp, h->colsq);
-    sigma_kernel<<<1, 128, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
+    sigma_kernel<<<1, 1024, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
     CPD_LAUNCH(h, "colsq/sigma");
     cpd_status s = gram_from(h, h->U[k], h->U[k], h->dims[k], h->sigma, 1, h->G[k]);
     if (s != CPD_OK) return s;
@@ -491,14 +497,12 @@ cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout) {
   return launch_pinv(h, jobs, 1);
 }
 
-cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P, double* B, int* tri) {
+cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P) {
   PinvJobs jobs;
   memset(&jobs, 0, sizeof(jobs));
   jobs.job[0].in[0] = G;
   jobs.job[0].nin = 1;
   jobs.job[0].out_pinv = P;
-  jobs.job[0].out_factor = B;
-  jobs.job[0].out_tri = tri;
   jobs.job[0].scratch = h->Gpart;
   return launch_pinv(h, jobs, 1);
 }
@@ -509,10 +513,15 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
   const int64_t I = h->dims[mode];
   {
     PhaseTimer pt(h, CPD_PHASE_SOLVE);
-    size_t shm = (size_t)(2 * R * R + TR * R) * sizeof(float);
-    solve_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+    size_t shm = (size_t)(2 * R * R) * sizeof(float);
+    if (R <= 32)
+      solve_kernel<32><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+    else if (R <= 64)
+      solve_kernel<64><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+    else
+      solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
     CPD_LAUNCH(h, "solve");
-    sigma_kernel<<<1, 128, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
+    sigma_kernel<<<1, 1024, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
     CPD_LAUNCH(h, "sigma");
   }
   if (out_sigma && out_sigma != h->sigma)
@@ -545,9 +554,11 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
   const int R = h->R;
   size_t s1 = (size_t)TR * R * sizeof(float);
   size_t s2 = (size_t)R * R * sizeof(double);
-  size_t s3 = (size_t)(2 * R * R + TR * R) * sizeof(float);
+  size_t s3 = (size_t)(2 * R * R) * sizeof(float);
   CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
   CPD_CUDA(h, cudaFuncSetAttribute(pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s2, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
   return CPD_OK;
 }

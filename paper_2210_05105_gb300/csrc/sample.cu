@@ -15,83 +15,73 @@ namespace {
 
 constexpr int LEV_THREADS = 256;
 
-// ell_i = || B u_i ||^2 with G_k^+ = B^T B (B lower triangular when G_k was
-// factored by Cholesky).  One row per thread; u_i in registers, B split into
-// float32 hi + lo in shared memory (every thread reads the same entry:
-// broadcast).  y = B u and ||y||^2 are accumulated in df64 on the float32
-// pipes (error-free products, TwoSum), i.e. to ~2^-48 relative instead of
-// float64 FMAs at 1/64 rate.  Also writes the sum of each block's scores.
-template <int RB>
+// ell_i = u_i^T X u_i with X = G_k^+ (Algorithm 2 line 2) as
+// sum_{a<=b} c_ab X_ab u_a u_b (c = 1 on the diagonal, 2 off it).  One warp
+// per row, lanes over the R(R+1)/2 pairs; the row and the coefficients
+// (split into float32 hi + lo) sit in shared memory.  Each product u_a u_b is
+// formed exactly (TwoProduct) and the sum is carried in df64 on the float32
+// pipes, i.e. to ~2^-48 relative instead of float64 FMAs at 1/64 rate.  A
+// block of 8 warps covers 256 consecutive rows and writes their sum.
 __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
-                                                          const double* __restrict__ B, const int* __restrict__ tri,
-                                                          double* __restrict__ ell, double* __restrict__ blk) {
-  extern __shared__ float Bsm[];     // hi: R x R, lo: R x R
-  __shared__ double red[LEV_THREADS / 32];
-  float* Bhi = Bsm;
-  float* Blo = Bsm + R * R;
-  const int t = threadIdx.x;
-  for (int e = t; e < R * R; e += LEV_THREADS) {
-    const double b = B[e];
-    const float hi = (float)b;
-    Bhi[e] = hi;
-    Blo[e] = (float)(b - (double)hi);
+                                                          const double* __restrict__ X, double* __restrict__ ell,
+                                                          double* __restrict__ blk) {
+  extern __shared__ float lsm[];
+  const int npairs = R * (R + 1) / 2;
+  float* Xhi = lsm;                          // npairs
+  float* Xlo = Xhi + npairs;                 // npairs
+  unsigned char* pa = reinterpret_cast<unsigned char*>(Xlo + npairs);
+  unsigned char* pb = pa + npairs;
+  float* us = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(lsm) + ((npairs * 10 + 15) & ~15));
+  __shared__ double wsum[LEV_THREADS / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  for (int p = t; p < npairs; p += LEV_THREADS) {
+    int a = 0, rem = p;
+    while (rem >= R - a) { rem -= R - a; ++a; }
+    const int b = a + rem;
+    const double x = (a == b ? 1.0 : 2.0) * X[a * R + b];
+    const float hi = (float)x;
+    Xhi[p] = hi;
+    Xlo[p] = (float)(x - (double)hi);
+    pa[p] = (unsigned char)a;
+    pb[p] = (unsigned char)b;
   }
-  const bool lower = *tri != 0;
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * LEV_THREADS + t;
-  double l = 0.0;
-  if (i < I) {
-    float u[RB];
-    const float4* row = reinterpret_cast<const float4*>(U + i * Rp);
-#pragma unroll
-    for (int q = 0; q < RB / 4; ++q) {
-      if (4 * q < Rp) {
-        float4 v = row[q];
-        u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
-      } else {
-        u[4 * q] = u[4 * q + 1] = u[4 * q + 2] = u[4 * q + 3] = 0.0f;
-      }
-    }
+  float* u = us + wid * Rp;
+  double wacc = 0.0;
+  const int64_t base = (int64_t)blockIdx.x * LEV_THREADS + wid * 32;
+  for (int rr = 0; rr < 32; ++rr) {
+    const int64_t i = base + rr;
+    if (i >= I) break;
+    for (int c = lane; c < Rp; c += 32) u[c] = U[i * Rp + c];
+    __syncwarp();
     float lh = 0.0f, ll = 0.0f;
-    if (lower) {
-#pragma unroll
-      for (int a = 0; a < RB; ++a) {
-        if (a < R) {
-          float yh = 0.0f, yl = 0.0f;
-#pragma unroll
-          for (int b = 0; b <= a; ++b) {
-            df_fma(yh, yl, Bhi[a * R + b], u[b]);
-            yl = __fmaf_rn(Blo[a * R + b], u[b], yl);
-          }
-          df_fma(lh, ll, yh, yh);
-          ll = __fmaf_rn(__fmul_rn(2.0f, yh), yl, ll);
-        }
-      }
-    } else {
-#pragma unroll 1
-      for (int a = 0; a < R; ++a) {
-        float yh = 0.0f, yl = 0.0f;
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-          if (b < R) {
-            df_fma(yh, yl, Bhi[a * R + b], u[b]);
-            yl = __fmaf_rn(Blo[a * R + b], u[b], yl);
-          }
-        }
-        df_fma(lh, ll, yh, yh);
-        ll = __fmaf_rn(__fmul_rn(2.0f, yh), yl, ll);
-      }
+    for (int p = lane; p < npairs; p += 32) {
+      const float ua = u[pa[p]], ub = u[pb[p]];
+      const float ph = __fmul_rn(ua, ub);
+      const float pl = __fmaf_rn(ua, ub, -ph);
+      const float xh = Xhi[p], xl = Xlo[p];
+      df_fma(lh, ll, ph, xh);
+      ll = __fmaf_rn(pl, xh, __fmaf_rn(ph, xl, ll));
     }
-    l = df_value(lh, ll);
-    ell[i] = l;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(CPD_FULL, lh, o);
+      const float ol = __shfl_xor_sync(CPD_FULL, ll, o);
+      float s, e;
+      df_two_sum(lh, oh, s, e);
+      lh = s;
+      ll = __fadd_rn(__fadd_rn(ll, ol), e);
+    }
+    const double l = df_value(lh, ll);
+    if (lane == 0) ell[i] = l;
+    wacc += l;
+    __syncwarp();
   }
-  // block sum in a fixed order
-  double s = warp_sum(l);
-  if ((t & 31) == 0) red[t >> 5] = s;
+  if (lane == 0) wsum[wid] = wacc;
   __syncthreads();
   if (t == 0) {
     double b = 0.0;
-    for (int w = 0; w < LEV_THREADS / 32; ++w) b += red[w];
+    for (int w = 0; w < LEV_THREADS / 32; ++w) b += wsum[w];
     blk[blockIdx.x] = b;
   }
 }
@@ -176,14 +166,17 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
   }
 }
 
-template <int RB>
+size_t lev_smem(int R) {
+  const int npairs = R * (R + 1) / 2;
+  return (size_t)((npairs * 10 + 15) & ~15) + (size_t)(LEV_THREADS / 32) * cpd_pad4(R) * 4;
+}
+
 cpd_status launch_lev(cpd_ctx* h, int k) {
   PhaseTimer pt(h, CPD_PHASE_SAMPLER);
   const int64_t I = h->dims[k];
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
-  size_t shm = (size_t)h->R * h->R * 2 * sizeof(float);
-  lev_kernel<RB><<<(unsigned)nb, LEV_THREADS, shm, h->stream>>>(h->U[k], I, h->R, h->Rp, h->Bk[k], h->Btri + k,
-                                                                 h->ell[k], h->blk[k]);
+  lev_kernel<<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(h->U[k], I, h->R, h->Rp, h->Gkpinv[k],
+                                                                       h->ell[k], h->blk[k]);
   CPD_LAUNCH(h, "lev");
   blk_scan_kernel<<<1, 32, 0, h->stream>>>(h->blk[k], nb);
   cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(h->ell[k], I, h->blk[k], h->cdf[k]);
@@ -196,11 +189,7 @@ cpd_status launch_lev(cpd_ctx* h, int k) {
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
 // once, outside any stream capture).
 cpd_status cpd_sample_init(cpd_ctx* h) {
-  int shm = h->R * h->R * (int)sizeof(double);
-  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem(h->R)));
   return CPD_OK;
 }
 
@@ -213,13 +202,9 @@ cpd_status cpd_sts_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long lon
 cpd_status cpd_refresh_sampler(cpd_ctx* h, int k) {
   if (h->opt.method == CPD_STS_CP) return cpd_sts_refresh(h, k);
   if (h->opt.method != CPD_ARLS_LEV) return CPD_OK;
-  cpd_status s = cpd_pinv_into(h, h->G[k], h->Gkpinv[k], h->Bk[k], h->Btri + k);
+  cpd_status s = cpd_pinv_into(h, h->G[k], h->Gkpinv[k]);
   if (s != CPD_OK) return s;
-  const int R = h->R;
-  if (R <= 32) return launch_lev<32>(h, k);
-  if (R <= 64) return launch_lev<64>(h, k);
-  if (R <= 96) return launch_lev<96>(h, k);
-  return launch_lev<128>(h, k);
+  return launch_lev(h, k);
 }
 
 cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep, unsigned long long sweep,
