@@ -207,6 +207,13 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
   hi = s;
   lo = __fadd_rn(lo, e);
 }
+// (h0, l0) += (h1, l1)
+__device__ __forceinline__ void df_merge(float& h0, float& l0, float h1, float l1) {
+  float s, e;
+  df_two_sum(h0, h1, s, e);
+  h0 = s;
+  l0 = __fadd_rn(__fadd_rn(l0, l1), e);
+}
 __device__ __forceinline__ double df_value(float hi, float lo) { return (double)hi + (double)lo; }
 
 #define CPD_STREAM_ARLS 0ull

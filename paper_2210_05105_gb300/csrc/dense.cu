@@ -99,15 +99,24 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
       }
     }
     __syncthreads();
+    // four independent df64 chains per pair (rows rr mod 4) for ILP
 #pragma unroll
     for (int m = 0; m < MAXP; ++m) {
       int p = t + m * DTHREADS;
       if (p < npairs) {
         const int a = pa[p], b = pb[p];
-        float hi = 0.0f, lo = 0.0f;
-#pragma unroll 8
-        for (int rr = 0; rr < TR; ++rr) df_fma(hi, lo, tile[rr * R + a], tile[rr * R + b]);
-        acc[m] += df_value(hi, lo);
+        float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f, h2 = 0.0f, l2 = 0.0f, h3 = 0.0f, l3 = 0.0f;
+#pragma unroll 4
+        for (int rr = 0; rr < TR; rr += 4) {
+          df_fma(h0, l0, tile[rr * R + a], tile[rr * R + b]);
+          df_fma(h1, l1, tile[(rr + 1) * R + a], tile[(rr + 1) * R + b]);
+          df_fma(h2, l2, tile[(rr + 2) * R + a], tile[(rr + 2) * R + b]);
+          df_fma(h3, l3, tile[(rr + 3) * R + a], tile[(rr + 3) * R + b]);
+        }
+        df_merge(h0, l0, h1, l1);
+        df_merge(h2, l2, h3, l3);
+        df_merge(h0, l0, h2, l2);
+        acc[m] += df_value(h0, l0);
       }
     }
     __syncthreads();
@@ -357,8 +366,8 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
       for (int cc = 0; cc < 32; ++cc) {
         const int c = c0 + cc;
         if (c < R) {
-          double sq = warp_sum((double)(out[cc] * out[cc]));
-          if (lane == 0) wsq[wid][c] += sq;
+          const float sq = warp_sum(live ? out[cc] * out[cc] : 0.0f);
+          if (lane == 0) wsq[wid][c] += (double)sq;
         }
       }
     }

@@ -16,72 +16,62 @@ namespace {
 constexpr int LEV_THREADS = 256;
 
 // ell_i = u_i^T X u_i with X = G_k^+ (Algorithm 2 line 2) as
-// sum_{a<=b} c_ab X_ab u_a u_b (c = 1 on the diagonal, 2 off it).  One warp
-// per row, lanes over the R(R+1)/2 pairs; the row and the coefficients
-// (split into float32 hi + lo) sit in shared memory.  Each product u_a u_b is
-// formed exactly (TwoProduct) and the sum is carried in df64 on the float32
-// pipes, i.e. to ~2^-48 relative instead of float64 FMAs at 1/64 rate.  A
-// block of 8 warps covers 256 consecutive rows and writes their sum.
+// sum_{a<=b} c_ab X_ab u_a u_b (c = 1 on the diagonal, 2 off it).  One row
+// per thread; the block's 256 rows sit column-major in shared memory
+// (conflict-free), the coefficients split into float32 hi + lo (all threads
+// read the same entry: broadcast).  Each product u_a u_b is formed exactly
+// (TwoProduct) and the sum is carried in df64 on the float32 pipes, i.e. to
+// ~2^-48 relative instead of float64 FMAs at 1/64 rate.  Also writes the sum
+// of each block's scores.
 __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
                                                           const double* __restrict__ X, double* __restrict__ ell,
                                                           double* __restrict__ blk) {
-  extern __shared__ float lsm[];
+  extern __shared__ float4 lsm4[];
   const int npairs = R * (R + 1) / 2;
-  float* Xhi = lsm;                          // npairs
-  float* Xlo = Xhi + npairs;                 // npairs
-  unsigned char* pa = reinterpret_cast<unsigned char*>(Xlo + npairs);
-  unsigned char* pb = pa + npairs;
-  float* us = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(lsm) + ((npairs * 10 + 15) & ~15));
-  __shared__ double wsum[LEV_THREADS / 32];
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  float2* Xs = reinterpret_cast<float2*>(lsm4);                 // npairs (hi, lo), row-major upper triangle
+  float* us = reinterpret_cast<float*>(Xs + npairs);            // Rp x 256, column c of row t at c * 256 + t
+  __shared__ double red[LEV_THREADS / 32];
+  const int t = threadIdx.x;
   for (int p = t; p < npairs; p += LEV_THREADS) {
     int a = 0, rem = p;
     while (rem >= R - a) { rem -= R - a; ++a; }
     const int b = a + rem;
     const double x = (a == b ? 1.0 : 2.0) * X[a * R + b];
     const float hi = (float)x;
-    Xhi[p] = hi;
-    Xlo[p] = (float)(x - (double)hi);
-    pa[p] = (unsigned char)a;
-    pb[p] = (unsigned char)b;
+    Xs[p] = make_float2(hi, (float)(x - (double)hi));
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * LEV_THREADS;
+  for (int e = t; e < LEV_THREADS * Rp; e += LEV_THREADS) {   // coalesced rows -> transposed tile
+    const int rr = e / Rp, c = e % Rp;
+    us[c * LEV_THREADS + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
   }
   __syncthreads();
-  float* u = us + wid * Rp;
-  double wacc = 0.0;
-  const int64_t base = (int64_t)blockIdx.x * LEV_THREADS + wid * 32;
-  for (int rr = 0; rr < 32; ++rr) {
-    const int64_t i = base + rr;
-    if (i >= I) break;
-    for (int c = lane; c < Rp; c += 32) u[c] = U[i * Rp + c];
-    __syncwarp();
+  const int64_t i = r0 + t;
+  double l = 0.0;
+  if (i < I) {
     float lh = 0.0f, ll = 0.0f;
-    for (int p = lane; p < npairs; p += 32) {
-      const float ua = u[pa[p]], ub = u[pb[p]];
-      const float ph = __fmul_rn(ua, ub);
-      const float pl = __fmaf_rn(ua, ub, -ph);
-      const float xh = Xhi[p], xl = Xlo[p];
-      df_fma(lh, ll, ph, xh);
-      ll = __fmaf_rn(pl, xh, __fmaf_rn(ph, xl, ll));
+    int p = 0;
+    for (int a = 0; a < R; ++a) {
+      const float ua = us[a * LEV_THREADS + t];
+      for (int b = a; b < R; ++b, ++p) {
+        const float ub = us[b * LEV_THREADS + t];
+        const float2 x = Xs[p];
+        const float ph = __fmul_rn(ua, ub);
+        const float pl = __fmaf_rn(ua, ub, -ph);
+        df_fma(lh, ll, ph, x.x);
+        ll = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll));
+      }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oh = __shfl_xor_sync(CPD_FULL, lh, o);
-      const float ol = __shfl_xor_sync(CPD_FULL, ll, o);
-      float s, e;
-      df_two_sum(lh, oh, s, e);
-      lh = s;
-      ll = __fadd_rn(__fadd_rn(ll, ol), e);
-    }
-    const double l = df_value(lh, ll);
-    if (lane == 0) ell[i] = l;
-    wacc += l;
-    __syncwarp();
+    l = df_value(lh, ll);
+    ell[i] = l;
   }
-  if (lane == 0) wsum[wid] = wacc;
+  // block sum in a fixed order
+  double s = warp_sum(l);
+  if ((t & 31) == 0) red[t >> 5] = s;
   __syncthreads();
   if (t == 0) {
     double b = 0.0;
-    for (int w = 0; w < LEV_THREADS / 32; ++w) b += wsum[w];
+    for (int w = 0; w < LEV_THREADS / 32; ++w) b += red[w];
     blk[blockIdx.x] = b;
   }
 }
@@ -168,7 +158,7 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
 
 size_t lev_smem(int R) {
   const int npairs = R * (R + 1) / 2;
-  return (size_t)((npairs * 10 + 15) & ~15) + (size_t)(LEV_THREADS / 32) * cpd_pad4(R) * 4;
+  return (size_t)npairs * 8 + (size_t)LEV_THREADS * cpd_pad4(R) * 4;
 }
 
 cpd_status launch_lev(cpd_ctx* h, int k) {
