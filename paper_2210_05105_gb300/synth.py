@@ -64,7 +64,7 @@ def coo_coordinates(dims, nnz, seed, zipf_s=0.0):
         _, first = np.unique(keys, return_index=True)
         if first.size >= nnz:
             keep = np.sort(first)[:nnz]
-            return drawn[:, keep].astype(np.int32)
+            return np.ascontiguousarray(drawn[:, keep], dtype=np.int32)
         need = nnz - first.size
         drawn = drawn[:, np.sort(first)]
 
@@ -102,6 +102,9 @@ WORKLOADS = {
     "small_uniform_200x150x100": dict(dims=(200, 150, 100), nnz=20_000, zipf=0.0,
                                       values="uniform", R=8, J=2000, sweeps=5,
                                       data_seed=1001, init_seed=2001, sample_seed=3001),
+    "zipf_1e5cube_5M": dict(dims=(100_000, 100_000, 100_000), nnz=5_000_000, zipf=1.1,
+                            values="lognormal", R=32, J=65536, sweeps=20,
+                            data_seed=1003, init_seed=2003, sample_seed=3003),
     "zipf_1e5cube_50M": dict(dims=(100_000, 100_000, 100_000), nnz=50_000_000, zipf=1.1,
                              values="lognormal", R=32, J=65536, sweeps=20,
                              data_seed=1002, init_seed=2002, sample_seed=3002),
