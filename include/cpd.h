@@ -207,6 +207,38 @@ cpd_status cpd_profile_read(cpd_handle h, double* ms, int64_t* launches);
  * cpd_als_sweep); memset and event nodes are not counted. */
 cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out);
 
+/*
+ * Downsampled MTTKRP without any device allocation (no counterpart in the
+ * paper; it restates Eq. 7 for callers that cannot allocate).  Meant for
+ * code that must not call cudaMalloc: work enqueued while a stream is being
+ * captured into a CUDA graph, code inside a framework whose memory pool
+ * already owns the device memory, and latency-bound callers that cannot
+ * accept the implicit device synchronisation of cudaMalloc / cudaFree.  It
+ * needs no cpd_handle (creating one allocates): the caller passes the COO
+ * tensor and the factor matrices directly, and one pass over the nonzeros
+ * picks those whose column was drawn.
+ *   N, dims (host), nnz, idx (N x nnz int32), vals    the tensor, as for cpd_create
+ *   factors  host array of N device pointers, U_k is I_k x R row-major float32
+ *            (row `mode` unused)
+ *   samp_idx N x J int32 drawn KRP rows (row `mode` ignored); w J float64 weights
+ *   Y        I_mode x R float32, overwritten
+ *   status_out device int32: set to 1 if some draw had an index out of range
+ *            (that draw is skipped), else 0
+ * Scratch: a fixed 2 MiB table in the library's static device memory, held on
+ * every GPU that loads the library until the process exits; J is limited to
+ * 65,536 (CPD_ERR_CAPACITY beyond).  The first call on a device looks up the
+ * table's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the table and it keeps the
+ * previous call's contents (each call clears it first), so calls whose GPU
+ * work overlaps -- on different streams, or host threads -- race and must be
+ * serialised by the caller.  Asynchronous on cuda_stream.
+ */
+cpd_status cpd_sampled_mttkrp_noalloc(int32_t N, const int64_t* dims, int64_t nnz,
+                                      const int32_t* idx, const float* vals,
+                                      const float* const* factors, int32_t R, int32_t mode,
+                                      const int32_t* samp_idx, const double* w, int64_t J,
+                                      float* Y, int32_t* status_out, void* cuda_stream);
+
 /* Wait for the handle's stream and return the first latched device error. */
 cpd_status cpd_synchronize(cpd_handle h);
 
