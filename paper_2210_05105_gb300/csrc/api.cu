@@ -114,7 +114,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_build_layouts(h)) != CPD_OK) return s;
 
   // ||T||^2
-  h->gram_blocks = h->num_sms * 2;
+  h->gram_blocks = h->num_sms * 4;
   const int npairs = R * (R + 1) / 2;
   if ((s = cpd_alloc(h, &h->Gpart, std::max((size_t)h->gram_blocks * npairs, 2 * (size_t)R * R))) != CPD_OK)
     return s;

@@ -15,7 +15,6 @@ namespace {
 
 constexpr int TR = 64;          // rows per tile
 constexpr int DTHREADS = 256;
-constexpr int MAXP = 33;        // ceil(128 * 129 / 2 / 256) Gram pairs per thread
 
 // ---- column sums of squares (float64 partials per block) ----------------
 // Thread (g, c) of a block accumulates column c over rows g, g+groups, ...
@@ -60,6 +59,7 @@ __global__ void sigma_kernel(const double* __restrict__ part, int nblk, int R, d
 // and float64 Gram partials of the stored float32 values.  Per 64-row tile a
 // thread accumulates its Gram entries as df64 sums of exact float32 products
 // (error ~ 64 * 2^-48 of the sum of |terms|), then adds them into float64.
+template <int MAXP>
 __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart) {
@@ -176,6 +176,116 @@ __device__ double block_sum_d(double v, double* red) {
   return r;
 }
 
+constexpr int PINV_FAST_R = 64;
+constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / DTHREADS;   // entries per thread
+
+// Fast path for R <= 64 on the float32 pipes: Gauss-Jordan in float32 gives
+// X0 ~ G^{-1}; Newton-Schulz steps X <- X + X (I - G X) with G X formed in
+// df64 (G split exactly into float32 hi + lo) and X carried as df64 bring X to
+// ~2^-48 relative.  Returns false (nothing written) when a float32 pivot is
+// below 1e-6 * max diag or the residual max |I - G X| does not fall below
+// 1e-10 within 6 steps; the float64 path then decides.
+__device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
+  __shared__ float rowk[PINV_FAST_R], colk[PINV_FAST_R];
+  __shared__ float red[DTHREADS / 32];
+  const int t = threadIdx.x;
+  const int RR = R * R;
+  float* Gh = sm;
+  float* Gl = Gh + RR;
+  float* Xh = Gl + RR;
+  float* Xl = Xh + RR;
+  float* W = Xl + RR;
+  for (int e = t; e < RR; e += DTHREADS) {
+    double v = 1.0;
+    for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
+    if (jb.out_had) jb.out_had[e] = v;
+    const float hi = (float)v;
+    Gh[e] = hi;
+    Gl[e] = (float)(v - (double)hi);
+    W[e] = hi;
+  }
+  __syncthreads();
+  float maxd = 0.0f;
+  for (int a = 0; a < R; ++a) maxd = fmaxf(maxd, fabsf(Gh[a * R + a]));
+  for (int k = 0; k < R; ++k) {
+    if (t < R) { rowk[t] = W[k * R + t]; colk[t] = W[t * R + k]; }
+    __syncthreads();
+    const float piv = rowk[k];
+    if (!(piv > 1e-6f * maxd) || !isfinite(piv)) return false;    // uniform
+    const float inv = 1.0f / piv;
+    for (int e = t; e < RR; e += DTHREADS) {
+      const int i = e / R, j = e % R;
+      float v;
+      if (i == k) v = (j == k) ? inv : rowk[j] * inv;
+      else if (j == k) v = -colk[i] * inv;
+      else v = fmaf(-colk[i], rowk[j] * inv, W[e]);
+      W[e] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < RR; e += DTHREADS) { Xh[e] = W[e]; Xl[e] = 0.0f; }
+  __syncthreads();
+  bool ok = false;
+  for (int it = 0; it < 6 && !ok; ++it) {
+    // W = I - G X with G X in df64
+    float emax = 0.0f;
+    for (int e = t; e < RR; e += DTHREADS) {
+      const int i = e / R, j = e % R;
+      float ah = 0.0f, al = 0.0f;
+      for (int k = 0; k < R; ++k) {
+        const float gh = Gh[i * R + k], gl = Gl[i * R + k], xh = Xh[k * R + j], xl = Xl[k * R + j];
+        df_fma(ah, al, gh, xh);
+        al = __fmaf_rn(gh, xl, __fmaf_rn(gl, xh, al));
+      }
+      const float ev = __fsub_rn(__fsub_rn(i == j ? 1.0f : 0.0f, ah), al);
+      W[e] = ev;
+      emax = fmaxf(emax, fabsf(ev));
+    }
+    emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 16));
+    emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 8));
+    emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 4));
+    emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 2));
+    emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 1));
+    if ((t & 31) == 0) red[t >> 5] = emax;
+    __syncthreads();
+    float em = 0.0f;
+    for (int w = 0; w < DTHREADS / 32; ++w) em = fmaxf(em, red[w]);
+    if (!isfinite(em)) return false;
+    // X <- X + X W (the correction is small: float32 suffices); once the
+    // residual is below 1e-10 this last step leaves X at the df64 noise level
+    float corr[PINV_PER_T];
+#pragma unroll
+    for (int m = 0; m < PINV_PER_T; ++m) {
+      const int e = t + m * DTHREADS;
+      float c = 0.0f;
+      if (e < RR) {
+        const int i = e / R, j = e % R;
+        for (int k = 0; k < R; ++k) c = fmaf(Xh[i * R + k], W[k * R + j], c);
+      }
+      corr[m] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < PINV_PER_T; ++m) {
+      const int e = t + m * DTHREADS;
+      if (e < RR) {
+        float sh, se;
+        df_two_sum(Xh[e], corr[m], sh, se);
+        Xl[e] = __fadd_rn(Xl[e], se);
+        Xh[e] = sh;
+      }
+    }
+    __syncthreads();
+    ok = em < 1e-10f;
+  }
+  if (!ok) return false;
+  for (int e = t; e < RR; e += DTHREADS) {
+    const int i = e / R, j = e % R;
+    jb.out_pinv[e] = 0.5 * (df_value(Xh[e], Xl[e]) + df_value(Xh[j * R + i], Xl[j * R + i]));
+  }
+  return true;
+}
+
 // Inverse of a symmetric positive definite G by Gauss-Jordan elimination
 // without pivoting (the pivots are the Cholesky / LDL^T pivots) when every
 // pivot exceeds 1e-9 * max diag; otherwise a parallel (round-robin) cyclic
@@ -191,6 +301,7 @@ __global__ void __launch_bounds__(DTHREADS) pinv_kernel(PinvJobs jobs, int R) {
   const PinvJob& jb = jobs.job[blockIdx.x];
   const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
+  if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A))) return;
   for (int e = t; e < RR; e += nt) {
     double v = 1.0;
     for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
@@ -310,66 +421,74 @@ __global__ void __launch_bounds__(DTHREADS) pinv_kernel(PinvJobs jobs, int R) {
 }
 
 // ---- solve: Uw = Y (P_hi + P_lo), float32 with the float64 G^+ split ----
-// One row per thread, the row of Y in registers, P in shared memory (all
-// threads read the same entry: broadcast); outputs in chunks of 32 columns
-// written as 16-byte vectors.  Column sums of squares: warp sums per row
-// batch into shared memory, then a fixed-order sum per block.
+// Four threads per row, each owning a quarter of the RB (>= Rp) columns;
+// the row of Y in registers, P_hi / P_lo in shared memory read as 16-byte
+// vectors (one load feeds four FMAs per thread).  Column sums of squares:
+// shuffles over the 8 rows a warp holds, then per-warp shared partials and a
+// fixed-order sum per block.
 template <int RB>
 __global__ void __launch_bounds__(DTHREADS) solve_kernel(
     const float* __restrict__ Y, const double* __restrict__ P, float* __restrict__ Uw, int64_t I, int R,
     int Rp, double* __restrict__ colpart) {
-  extern __shared__ float sm[];
-  float* Phi = sm;                 // R x R
-  float* Plo = sm + R * R;         // R x R
+  constexpr int CPT = RB / 4;          // columns per thread
+  extern __shared__ float4 sm4[];
+  float* Phi = reinterpret_cast<float*>(sm4);   // R x RB, zero past R
+  float* Plo = Phi + R * RB;
   __shared__ double wsq[DTHREADS / 32][CPD_MAX_RANK];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  for (int e = t; e < R * R; e += DTHREADS) {
-    const double p = P[e];
+  const int q = t & 3, rl = t >> 2;
+  for (int e = t; e < R * RB; e += DTHREADS) {
+    const int a = e / RB, c = e % RB;
+    const double p = c < R ? P[a * R + c] : 0.0;
     const float hi = (float)p;
     Phi[e] = hi;
     Plo[e] = (float)(p - (double)hi);
   }
   for (int c = lane; c < CPD_MAX_RANK; c += 32) wsq[wid][c] = 0.0;
   __syncthreads();
-  for (int64_t r0 = (int64_t)blockIdx.x * DTHREADS; r0 < I; r0 += (int64_t)gridDim.x * DTHREADS) {
-    const int64_t i = r0 + t;
+  const int c0 = q * CPT;
+  for (int64_t r0 = (int64_t)blockIdx.x * (DTHREADS / 4); r0 < I; r0 += (int64_t)gridDim.x * (DTHREADS / 4)) {
+    const int64_t i = r0 + rl;
     const bool live = i < I;
     float y[RB];
     const float4* yrow = reinterpret_cast<const float4*>(Y + (live ? i : 0) * Rp);
 #pragma unroll
-    for (int q = 0; q < RB / 4; ++q) {
-      float4 v = (live && 4 * q < Rp) ? yrow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-      y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
+    for (int v = 0; v < RB / 4; ++v) {
+      const float4 x = (live && 4 * v < Rp) ? yrow[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      y[4 * v] = x.x; y[4 * v + 1] = x.y; y[4 * v + 2] = x.z; y[4 * v + 3] = x.w;
     }
-    for (int c0 = 0; c0 < Rp; c0 += 32) {
-      float out[32];
+    float out[CPT];
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) out[cc] = 0.0f;
+    for (int cc = 0; cc < CPT; ++cc) out[cc] = 0.0f;
 #pragma unroll
-      for (int a = 0; a < RB; ++a) {
-        if (a < R) {
-          const float ya = y[a];
+    for (int a = 0; a < RB; ++a) {
+      if (a < R) {
+        const float ya = y[a];
+        const float4* ph = reinterpret_cast<const float4*>(Phi + a * RB + c0);
+        const float4* pl = reinterpret_cast<const float4*>(Plo + a * RB + c0);
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc) {
-            const int c = c0 + cc;
-            if (c < R) out[cc] = fmaf(ya, Phi[a * R + c], fmaf(ya, Plo[a * R + c], out[cc]));
-          }
+        for (int v = 0; v < CPT / 4; ++v) {
+          const float4 h4 = ph[v], l4 = pl[v];
+          out[4 * v] = fmaf(ya, h4.x, fmaf(ya, l4.x, out[4 * v]));
+          out[4 * v + 1] = fmaf(ya, h4.y, fmaf(ya, l4.y, out[4 * v + 1]));
+          out[4 * v + 2] = fmaf(ya, h4.z, fmaf(ya, l4.z, out[4 * v + 2]));
+          out[4 * v + 3] = fmaf(ya, h4.w, fmaf(ya, l4.w, out[4 * v + 3]));
         }
       }
-      if (live) {
-        float4* urow = reinterpret_cast<float4*>(Uw + i * Rp + c0);
+    }
+    if (live) {
+      float4* urow = reinterpret_cast<float4*>(Uw + i * Rp + c0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (c0 + 4 * q < Rp) urow[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-      }
+      for (int v = 0; v < CPT / 4; ++v)
+        if (c0 + 4 * v < Rp) urow[v] = make_float4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+    }
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) {
-        const int c = c0 + cc;
-        if (c < R) {
-          const float sq = warp_sum(live ? out[cc] * out[cc] : 0.0f);
-          if (lane == 0) wsq[wid][c] += (double)sq;
-        }
-      }
+    for (int cc = 0; cc < CPT; ++cc) {
+      float sq = live ? out[cc] * out[cc] : 0.0f;
+      sq += __shfl_xor_sync(CPD_FULL, sq, 4);
+      sq += __shfl_xor_sync(CPD_FULL, sq, 8);
+      sq += __shfl_xor_sync(CPD_FULL, sq, 16);
+      if (lane < 4 && c0 + cc < R) wsq[wid][c0 + cc] += (double)sq;
     }
   }
   __syncthreads();
@@ -379,6 +498,8 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
     colpart[(int64_t)blockIdx.x * R + c] = s;
   }
 }
+
+static int solve_rb(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
 
 // ---- fit ------------------------------------------------------------------
 struct FitArgs {
@@ -459,8 +580,20 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
   const int R = h->R;
   PhaseTimer pt(h, CPD_PHASE_GRAM);
   size_t shm = (size_t)TR * R * sizeof(float);
-  normalize_gram_kernel<<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
-                                                                      h->Gpart);
+  const int npairs = R * (R + 1) / 2;
+  // Gram entries per thread: ceil(npairs / 256) rounded up to 1, 3, 9 or 33
+  if (npairs <= DTHREADS)
+    normalize_gram_kernel<1><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
+                                                                           h->Gpart);
+  else if (npairs <= 3 * DTHREADS)
+    normalize_gram_kernel<3><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
+                                                                           h->Gpart);
+  else if (npairs <= 9 * DTHREADS)
+    normalize_gram_kernel<9><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
+                                                                           h->Gpart);
+  else
+    normalize_gram_kernel<33><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
+                                                                            h->Gpart);
   CPD_LAUNCH(h, "normalize_gram");
   gram_reduce_kernel<<<std::max(1, (R * (R + 1) / 2 + 7) / 8), 256, 0, h->stream>>>(h->Gpart, h->gram_blocks, R, G);
   CPD_LAUNCH(h, "gram_reduce");
@@ -484,10 +617,16 @@ cpd_status cpd_renormalize_inputs(cpd_ctx* h) {
   return CPD_OK;
 }
 
+static size_t pinv_smem(int R) {
+  size_t slow = (size_t)R * R * sizeof(double);
+  size_t fast = R <= PINV_FAST_R ? (size_t)5 * R * R * sizeof(float) : 0;
+  return std::max(slow, fast);
+}
+
 static cpd_status launch_pinv(cpd_ctx* h, const PinvJobs& jobs, int njobs) {
   PhaseTimer pt(h, CPD_PHASE_PINV);
   const int R = h->R;
-  size_t shm = (size_t)R * R * sizeof(double);
+  size_t shm = pinv_smem(R);
   pinv_kernel<<<njobs, DTHREADS, shm, h->stream>>>(jobs, R);
   CPD_LAUNCH(h, "pinv");
   return CPD_OK;
@@ -522,10 +661,13 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
   const int64_t I = h->dims[mode];
   {
     PhaseTimer pt(h, CPD_PHASE_SOLVE);
-    size_t shm = (size_t)(2 * R * R) * sizeof(float);
-    if (R <= 32)
+    const int rb = solve_rb(R);
+    size_t shm = (size_t)(2 * R * rb) * sizeof(float);
+    if (rb == 16)
+      solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+    else if (rb == 32)
       solve_kernel<32><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
-    else if (R <= 64)
+    else if (rb == 64)
       solve_kernel<64><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
     else
       solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
@@ -562,10 +704,14 @@ cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out) {
 cpd_status cpd_dense_init(cpd_ctx* h) {
   const int R = h->R;
   size_t s1 = (size_t)TR * R * sizeof(float);
-  size_t s2 = (size_t)R * R * sizeof(double);
-  size_t s3 = (size_t)(2 * R * R) * sizeof(float);
-  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
+  size_t s2 = pinv_smem(R);
+  size_t s3 = (size_t)(2 * R * solve_rb(R)) * sizeof(float);
+  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<33>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
   CPD_CUDA(h, cudaFuncSetAttribute(pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s2, 1)));
+  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
   CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
   CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
   CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));

@@ -155,17 +155,35 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
   const int q = C >= 32 ? lane : lane % C;
   for (int64_t c = warp; c < nchunks; c += nwarps) {
     const int64_t p = c * 32 + lane;
+    // The 32 positions of the chunk meet at most 32 consecutive segments:
+    // one search finds the first, the window of their offsets goes to the
+    // lanes, and each lane locates its own segment in the window by shuffles.
+    uint32_t seg0 = 0;
+    if (lane == 0) {
+      uint32_t lo = 0, hi = nu - 1;        // last segment with offset <= c * 32
+      const uint32_t p0 = (uint32_t)(c * 32);
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (a.uq_off[mid] <= p0) lo = mid; else hi = mid - 1;
+      }
+      seg0 = lo;
+    }
+    seg0 = __shfl_sync(CPD_FULL, seg0, 0);
+    const uint32_t wseg = seg0 + lane;
+    const uint32_t woff = wseg < nu ? a.uq_off[wseg] : 0xffffffffu;
+    uint32_t loc = 0;                      // last window slot with offset <= p
+#pragma unroll
+    for (int b = 16; b > 0; b >>= 1) {
+      const uint32_t o = __shfl_sync(CPD_FULL, woff, (int)(loc + b));
+      if (o <= (uint32_t)p) loc += b;
+    }
+    const uint32_t segoff = __shfl_sync(CPD_FULL, woff, (int)loc);
     uint32_t row = 0, useg = 0;
     float scale = 0.0f;
     if (p < total) {
-      uint32_t lo = 0, hi = nu - 1;        // last segment with offset <= p
-      while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (a.uq_off[mid] <= (uint32_t)p) lo = mid; else hi = mid - 1;
-      }
-      useg = lo;
-      const uint32_t slot = a.uq_slot[lo];
-      const uint32_t e = a.dd_tag[slot] + ((uint32_t)p - a.uq_off[lo]);
+      useg = seg0 + loc;
+      const uint32_t slot = a.uq_slot[useg];
+      const uint32_t e = a.dd_tag[slot] + ((uint32_t)p - segoff);
       const uint2 en = a.ent[e];
       row = en.x;
       scale = (float)(a.dd_w[slot] * (double)__uint_as_float(en.y));

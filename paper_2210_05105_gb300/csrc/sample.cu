@@ -22,14 +22,15 @@ constexpr int LEV_THREADS = 256;
 // read the same entry: broadcast).  Each product u_a u_b is formed exactly
 // (TwoProduct) and the sum is carried in df64 on the float32 pipes, i.e. to
 // ~2^-48 relative instead of float64 FMAs at 1/64 rate.  Also writes the sum
-// of each block's scores.
+// of each block's scores.  (The tile's row stride 257 keeps the transposing
+// stores free of bank conflicts.)
 __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
                                                           const double* __restrict__ X, double* __restrict__ ell,
                                                           double* __restrict__ blk) {
   extern __shared__ float4 lsm4[];
   const int npairs = R * (R + 1) / 2;
   float2* Xs = reinterpret_cast<float2*>(lsm4);                 // npairs (hi, lo), row-major upper triangle
-  float* us = reinterpret_cast<float*>(Xs + npairs);            // Rp x 256, column c of row t at c * 256 + t
+  float* us = reinterpret_cast<float*>(Xs + npairs);            // Rp x 257: column c of row t at c * 257 + t
   __shared__ double red[LEV_THREADS / 32];
   const int t = threadIdx.x;
   for (int p = t; p < npairs; p += LEV_THREADS) {
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
   const int64_t r0 = (int64_t)blockIdx.x * LEV_THREADS;
   for (int e = t; e < LEV_THREADS * Rp; e += LEV_THREADS) {   // coalesced rows -> transposed tile
     const int rr = e / Rp, c = e % Rp;
-    us[c * LEV_THREADS + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
+    us[c * (LEV_THREADS + 1) + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
   }
   __syncthreads();
   const int64_t i = r0 + t;
@@ -52,9 +53,9 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
     float lh = 0.0f, ll = 0.0f;
     int p = 0;
     for (int a = 0; a < R; ++a) {
-      const float ua = us[a * LEV_THREADS + t];
+      const float ua = us[a * (LEV_THREADS + 1) + t];
       for (int b = a; b < R; ++b, ++p) {
-        const float ub = us[b * LEV_THREADS + t];
+        const float ub = us[b * (LEV_THREADS + 1) + t];
         const float2 x = Xs[p];
         const float ph = __fmul_rn(ua, ub);
         const float pl = __fmaf_rn(ua, ub, -ph);
@@ -158,7 +159,7 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
 
 size_t lev_smem(int R) {
   const int npairs = R * (R + 1) / 2;
-  return (size_t)npairs * 8 + (size_t)LEV_THREADS * cpd_pad4(R) * 4;
+  return (size_t)npairs * 8 + (size_t)(LEV_THREADS + 1) * cpd_pad4(R) * 4;
 }
 
 cpd_status launch_lev(cpd_ctx* h, int k) {
