@@ -116,13 +116,22 @@ def dist():
 
 
 def allreduce_max(x, world):
+    """Max of x over the replicas (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as tdist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(world, steps, local_ms):
+    """Whole-job sweeps/s of `world` independent replicas that each ran
+    `steps` sweeps in local_ms: all sweeps / the slowest replica's time."""
+    slowest = allreduce_max(local_ms, world)
+    return world * steps / (slowest / 1e3), slowest
 
 
 def barrier(world):
@@ -223,8 +232,7 @@ def ours(args, world, rank, local):
     barrier(world)
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
-    total_ms = allreduce_max(sum(step_ms), world)
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = replica_throughput(world, args.steps, sum(step_ms))
     launches_per_step = cpd.cpd_sweep_kernel_count(h)
     fit = cpd.cpd_fit(h)
 

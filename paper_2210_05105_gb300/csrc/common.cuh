@@ -69,6 +69,9 @@ struct cpd_ctx {
   double* sts_ggt[CPD_MAX_MODES] = {nullptr}; // R x R: G^+ (*) Grams of factors drawn after k
   double* sts_Z = nullptr;                    // <G^+, G>_F
   float* sts_h = nullptr;                     // J x Rp running Hadamard products
+  double* sts_q = nullptr;                    // Imax: row masses of the first factor drawn
+  double* sts_cdf = nullptr;                  // Imax: their running sums
+  double* sts_blk = nullptr;                  // block sums
 
   // per-update work buffers
   double* Gn = nullptr;        // R x R Hadamard of Grams for the solved mode
@@ -233,6 +236,8 @@ cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out);
 // sample.cu
 cpd_status cpd_refresh_sampler(cpd_ctx* h, int mode);
 cpd_status cpd_sample_init(cpd_ctx* h);
+cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
+                            double* cdf);
 cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep,
                     unsigned long long sweep, int32_t* out_idx, double* out_p, double* out_w);
 // mttkrp.cu

@@ -162,20 +162,30 @@ size_t lev_smem(int R) {
   return (size_t)npairs * 8 + (size_t)(LEV_THREADS + 1) * cpd_pad4(R) * 4;
 }
 
-cpd_status launch_lev(cpd_ctx* h, int k) {
-  PhaseTimer pt(h, CPD_PHASE_SAMPLER);
-  const int64_t I = h->dims[k];
+cpd_status quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
+                        double* cdf) {
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
-  lev_kernel<<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(h->U[k], I, h->R, h->Rp, h->Gkpinv[k],
-                                                                       h->ell[k], h->blk[k]);
+  lev_kernel<<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk);
   CPD_LAUNCH(h, "lev");
-  blk_scan_kernel<<<1, 32, 0, h->stream>>>(h->blk[k], nb);
-  cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(h->ell[k], I, h->blk[k], h->cdf[k]);
+  blk_scan_kernel<<<1, 32, 0, h->stream>>>(blk, nb);
+  cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(q, I, blk, cdf);
   CPD_LAUNCH(h, "cdf");
   return CPD_OK;
 }
 
+cpd_status launch_lev(cpd_ctx* h, int k) {
+  PhaseTimer pt(h, CPD_PHASE_SAMPLER);
+  return quadform_cdf(h, h->U[k], h->dims[k], h->Gkpinv[k], h->ell[k], h->blk[k], h->cdf[k]);
+}
+
 }  // namespace
+
+// q[i] = U[i] X U[i]^T for symmetric X (df64), block sums, and the inclusive
+// float64 running sums cdf (used by CP-ARLS-LEV and by the first STS factor).
+cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
+                            double* cdf) {
+  return quadform_cdf(h, U, I, X, q, blk, cdf);
+}
 
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
 // once, outside any stream capture).

@@ -258,6 +258,44 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
   }
 }
 
+// The first factor drawn has h = 1, so its conditional row masses
+// q_i = U_k[i] G_{>k} U_k[i]^T are the same for every draw and the tree's node
+// masses are partial sums of them: the walk is an inverse CDF over q
+// (computed once, in df64, by cpd_quadform_cdf).  One thread per draw.
+__global__ void sts_first_kernel(const double* __restrict__ cdf, const double* __restrict__ q, int64_t I,
+                                 const float* __restrict__ U, int Rp, float* __restrict__ Hs,
+                                 int32_t* __restrict__ out_idx, double* __restrict__ out_p, double* __restrict__ out_w,
+                                 const double* __restrict__ Zp, int last, int k, int n, int64_t J,
+                                 unsigned long long seed, const unsigned long long* __restrict__ d_sweep,
+                                 unsigned long long h_sweep) {
+  const unsigned long long s = d_sweep ? *d_sweep : h_sweep;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
+    const double C = cdf[I - 1];
+    const double t = cpd_uniform(seed, CPD_STREAM_STS, (unsigned long long)j, (unsigned long long)k,
+                                 (unsigned long long)n, s) * C;
+    int64_t lo = 0, hi = I;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+    }
+    if (lo >= I) {
+      lo = I - 1;
+      while (lo > 0 && !(q[lo] > 0.0)) --lo;
+    }
+    out_idx[(int64_t)k * J + j] = (int32_t)lo;
+    out_idx[(int64_t)n * J + j] = -1;
+    if (last) {
+      const double prob = q[lo] / *Zp;
+      if (out_p) out_p[j] = prob;
+      if (out_w) out_w[j] = 1.0 / ((double)J * prob);
+    } else {
+      const float4* src = reinterpret_cast<const float4*>(U + lo * Rp);
+      float4* dst = reinterpret_cast<float4*>(Hs + j * Rp);
+      for (int v = 0; v < Rp / 4; ++v) dst[v] = src[v];
+    }
+  }
+}
+
 size_t sts_smem(int R, int F) {
   const int npairs = R * (R + 1) / 2;
   const int npad = (npairs + 3) & ~3;
@@ -295,6 +333,9 @@ cpd_status cpd_sts_alloc(cpd_ctx* h) {
   }
   if ((s = cpd_alloc(h, &h->sts_Z, 1)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_h, (size_t)std::max<int64_t>(h->opt.samples, 1) * h->Rp)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->sts_q, (size_t)h->Imax)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->sts_cdf, (size_t)h->Imax)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->sts_blk, (size_t)cpd_ceil_div(h->Imax, 256))) != CPD_OK) return s;
   const int shm = (int)sts_smem(R, h->F);
   CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
   CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
@@ -338,6 +379,16 @@ cpd_status cpd_sts_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long lon
     if (k != mode) { if (firstk < 0) firstk = k; lastk = k; }
   for (int k = 0; k < h->N; ++k) {
     if (k == mode) continue;
+    if (k == firstk) {
+      cpd_status s = cpd_quadform_cdf(h, h->U[k], h->dims[k], h->sts_ggt[k], h->sts_q, h->sts_blk, h->sts_cdf);
+      if (s != CPD_OK) return s;
+      const int grid = (int)std::min<int64_t>(cpd_ceil_div(J, 256), (int64_t)h->num_sms * 8);
+      sts_first_kernel<<<grid, 256, 0, h->stream>>>(h->sts_cdf, h->sts_q, h->dims[k], h->U[k], h->Rp, h->sts_h,
+                                                    out_idx, out_p, out_w, h->sts_Z, k == lastk, k, mode, J,
+                                                    h->opt.seed, d_sweep, sweep);
+      CPD_LAUNCH(h, "sts_first");
+      continue;
+    }
     StsArgs a;
     memset(&a, 0, sizeof(a));
     a.tree = h->tree32[k]; a.U = h->U[k]; a.Ggt = h->sts_ggt[k]; a.Z = h->sts_Z; a.Hs = h->sts_h;
