@@ -72,7 +72,11 @@ typedef struct {
   int32_t leaf_rows;       /* STS-CP rows per tree leaf F; 0 means F = R */
   int32_t input_on_host;   /* 1: idx, vals, init_factors of cpd_create are host memory */
   int64_t reserved_i64[4];
-  int32_t reserved_i32[8];
+  int32_t sketched_gram;   /* 0: solve with G = *_{k!=n} U_k^T U_k (Eq. 5, Sec. 4);
+                              1: with the Gram of the sampled rows, sum_j w_j h_j h_j^T,
+                              i.e. the normal equations of the downsampled problem
+                              (Fig. 2 bottom, G~^+) */
+  int32_t reserved_i32[7];
 } cpd_options;
 
 /* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */
@@ -141,6 +145,8 @@ cpd_status cpd_exact_mttkrp(cpd_handle h, int32_t mode, float* Y);
  * sampler (Algorithm 2 or 4).
  *   Y          I_mode x R float32 (may be the buffer given to cpd_sampled_mttkrp).
  *   out_sigma  R float64, or NULL.
+ * With options.sketched_gram = 1 the Gram is that of the draws passed to the
+ * last cpd_sampled_mttkrp call for this mode (sum_j w_j h_j h_j^T).
  */
 cpd_status cpd_gram_solve(cpd_handle h, int32_t mode, const float* Y, double* out_sigma);
 

@@ -428,18 +428,27 @@ def fit(idx, vals, factors, sigma):
 # ALS driver (Algorithm 1)
 # ---------------------------------------------------------------------------
 
+def sketched_gram(factors, n, samp_idx, w):
+    """Gram of the downsampled design matrix, (S U_{!=n})^T (S U_{!=n}) =
+    sum_j w_j h_j h_j^T over the draws (the G~ of Fig. 2, bottom)."""
+    h = krp_rows(factors, samp_idx, n)
+    return h.T @ (np.asarray(w, dtype=np.float64)[:, None] * h)
+
+
 def sample_weights(p, J):
     """w_j = 1 / (J p_j): diagonal of S^T S for i.i.d. draws with probability p_j."""
     return 1.0 / (J * np.asarray(p, dtype=np.float64))
 
 
-def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None):
+def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None, sketched=False):
     """One subproblem of Algorithm 1 (lines 6-8) for mode n; updates state.
 
     state: dict with idx, vals, dims, factors (list of (I_k, R) float64),
     sigma, grams, and per method the sampler structures.
     Returns a dict of the intermediate quantities (samples, Y, G^+) so that
-    tests can compare every step.
+    tests can compare every step.  sketched=True solves with the Gram of the
+    drawn rows (the downsampled normal equations of Fig. 2, bottom) instead of
+    the Hadamard product of the factor Grams (Eq. 5).
     """
     idx, vals, dims, factors = state["idx"], state["vals"], state["dims"], state["factors"]
     grams = state["grams"]
@@ -458,6 +467,9 @@ def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None):
         w = sample_weights(p, J)
         Y = sampled_mttkrp(idx, vals, dims, factors, n, sidx, w)
         out.update({"samp_idx": sidx, "p": p, "w": w, "near_tie": near})
+        if sketched:
+            Gp = pinv_sym(sketched_gram(factors, n, sidx, w))
+            out["Gpinv"] = Gp
     Un, sigma = solve_and_renorm(Y, Gp)
     out.update({"Y": Y, "U": Un, "sigma": sigma})
     factors[n] = Un
@@ -489,12 +501,12 @@ def als_init(idx, vals, dims, init_factors, method, leaf_rows=None):
     return state
 
 
-def als(idx, vals, dims, init_factors, method, sweeps, J=0, seed=0, leaf_rows=None):
+def als(idx, vals, dims, init_factors, method, sweeps, J=0, seed=0, leaf_rows=None, sketched=False):
     """Run Algorithm 1 for `sweeps` rounds; returns (state, per-sweep fits)."""
     state = als_init(idx, vals, dims, init_factors, method, leaf_rows)
     fits = []
     for s in range(sweeps):
         for n in range(len(dims)):
-            als_mode_update(state, n, method, J, seed, s, leaf_rows)
+            als_mode_update(state, n, method, J, seed, s, leaf_rows, sketched)
         fits.append(fit(state["idx"], state["vals"], state["factors"], state["sigma"]))
     return state, fits

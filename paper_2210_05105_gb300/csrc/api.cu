@@ -58,6 +58,8 @@ cpd_status mode_update(cpd_ctx* h, int n) {
     if ((s = cpd_sampled_mttkrp_launch(h, n, h->samp_idx, h->samp_w, h->samp_p, J, h->Y, nullptr)) != CPD_OK)
       return s;
   }
+  if (h->opt.sketched_gram && h->opt.method != CPD_EXACT && (s = cpd_pinv_into(h, h->Gsk, h->Gnpinv)) != CPD_OK)
+    return s;
   if ((s = cpd_solve_renorm(h, n, h->Y, nullptr)) != CPD_OK) return s;
   return cpd_refresh_sampler(h, n);
 }
@@ -145,6 +147,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   }
   if ((s = cpd_alloc(h, &h->sigma, (size_t)R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Gn, (size_t)R * R)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->Gsk, (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Gnpinv, (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Y, (size_t)h->Imax * Rp)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Uwork, (size_t)h->Imax * Rp)) != CPD_OK) return s;
@@ -160,7 +163,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_alloc(h, &h->dd_tag, dcap)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->dd_w, dcap)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->uq_slot, (size_t)h->Jcap)) != CPD_OK) return s;
-  if ((s = cpd_alloc(h, &h->uq_len, (size_t)h->Jcap)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->chunk_seg, (size_t)cpd_ceil_div(std::max<int64_t>(nnz, 1), 32) + 1)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->uq_off, (size_t)h->Jcap + 1)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->H, (size_t)h->Jcap * Rp)) != CPD_OK) return s;
 
@@ -274,7 +277,9 @@ cpd_status cpd_gram_solve(cpd_handle h, int32_t mode, const float* Y, double* ou
   cpd_status s;
   if (h->Rp != h->R) CPD_CUDA(h, cudaMemsetAsync(h->Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), h->stream));
   if ((s = copy_rows(h, h->Y, h->Rp, Y, h->R, h->dims[mode], h->R)) != CPD_OK) return s;
-  if ((s = cpd_hadamard_pinv(h, mode, h->Gn, h->Gnpinv)) != CPD_OK) return s;
+  if (h->opt.sketched_gram && h->opt.method != CPD_EXACT) s = cpd_pinv_into(h, h->Gsk, h->Gnpinv);
+  else s = cpd_hadamard_pinv(h, mode, h->Gn, h->Gnpinv);
+  if (s != CPD_OK) return s;
   if ((s = cpd_solve_renorm(h, mode, h->Y, out_sigma)) != CPD_OK) return s;
   return cpd_refresh_sampler(h, mode);
 }

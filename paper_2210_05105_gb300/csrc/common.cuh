@@ -74,6 +74,7 @@ struct cpd_ctx {
   double* sts_blk = nullptr;                  // block sums
 
   // per-update work buffers
+  double* Gsk = nullptr;       // R x R Gram of the last draws (sketched-Gram solve)
   double* Gn = nullptr;        // R x R Hadamard of Grams for the solved mode
   double* Gnpinv = nullptr;    // R x R its pseudo-inverse
   double* Gpart = nullptr;     // Gram partial sums: gram_blocks x R x R
@@ -89,12 +90,12 @@ struct cpd_ctx {
   int64_t Jcap = 0;
   uint32_t dedup_mask = 0;
   uint32_t* dd_tag = nullptr;  // dedup capacity: fiber begin offset or EMPTY
-  double* dd_w = nullptr;      // summed weight per distinct sampled column
+  float* dd_w = nullptr;       // summed weight per distinct sampled column
   uint32_t* uq_slot = nullptr; // Jcap: dedup slot of each distinct column
-  uint32_t* uq_len = nullptr;  // Jcap
-  uint32_t* uq_off = nullptr;  // Jcap + 1 exclusive offsets into the flat list
+  uint32_t* chunk_seg = nullptr; // ceil(nnz / 32): distinct column holding the first nonzero of each chunk
+  uint32_t* uq_off = nullptr;  // Jcap: offset of each distinct column's nonzeros in the flat list
   float* H = nullptr;          // Jcap x Rp: KRP row of each distinct column
-  uint32_t* counters = nullptr;// [0] distinct columns, [1] nnz_sel (low), [2..] spare
+  uint32_t* counters = nullptr;// words 0-1: one 64-bit (distinct columns << 32 | nnz_sel)
   int* status = nullptr;       // latched device error (cpd_status)
   double* fit_out = nullptr;   // 2 doubles: <T, T~>, ||T~||^2
   unsigned long long* sweep_ctr = nullptr;  // device sweep counter for graphs
@@ -228,6 +229,7 @@ cpd_status cpd_build_layouts(cpd_ctx* h);
 // dense.cu
 cpd_status cpd_renormalize_inputs(cpd_ctx* h);
 cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G);
+cpd_status cpd_sketch_gram(cpd_ctx* h, int mode, const int32_t* idx, const double* w, int64_t J);
 cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout);
 cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P);
 cpd_status cpd_dense_init(cpd_ctx* h);

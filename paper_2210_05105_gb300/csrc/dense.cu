@@ -80,9 +80,14 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     pb[p] = (unsigned char)(a + rem);
   }
   __syncthreads();
-  double acc[MAXP];
+  // df64 accumulators (4 chains per entry for ILP) live across all tiles of
+  // the block: a block holds ~I / gridDim rows, so the df64 error stays near
+  // (rows per block) * 2^-48 of the sum of |terms|; float64 only at the end.
+  float ah[MAXP][4], al[MAXP][4];
 #pragma unroll
-  for (int m = 0; m < MAXP; ++m) acc[m] = 0.0;
+  for (int m = 0; m < MAXP; ++m)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { ah[m][c] = 0.0f; al[m][c] = 0.0f; }
   const int64_t ntiles = cpd_ceil_div(I, TR);
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t r0 = tl * TR;
@@ -99,24 +104,18 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
       }
     }
     __syncthreads();
-    // four independent df64 chains per pair (rows rr mod 4) for ILP
 #pragma unroll
     for (int m = 0; m < MAXP; ++m) {
       int p = t + m * DTHREADS;
       if (p < npairs) {
         const int a = pa[p], b = pb[p];
-        float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f, h2 = 0.0f, l2 = 0.0f, h3 = 0.0f, l3 = 0.0f;
 #pragma unroll 4
         for (int rr = 0; rr < TR; rr += 4) {
-          df_fma(h0, l0, tile[rr * R + a], tile[rr * R + b]);
-          df_fma(h1, l1, tile[(rr + 1) * R + a], tile[(rr + 1) * R + b]);
-          df_fma(h2, l2, tile[(rr + 2) * R + a], tile[(rr + 2) * R + b]);
-          df_fma(h3, l3, tile[(rr + 3) * R + a], tile[(rr + 3) * R + b]);
+          df_fma(ah[m][0], al[m][0], tile[rr * R + a], tile[rr * R + b]);
+          df_fma(ah[m][1], al[m][1], tile[(rr + 1) * R + a], tile[(rr + 1) * R + b]);
+          df_fma(ah[m][2], al[m][2], tile[(rr + 2) * R + a], tile[(rr + 2) * R + b]);
+          df_fma(ah[m][3], al[m][3], tile[(rr + 3) * R + a], tile[(rr + 3) * R + b]);
         }
-        df_merge(h0, l0, h1, l1);
-        df_merge(h2, l2, h3, l3);
-        df_merge(h0, l0, h2, l2);
-        acc[m] += df_value(h0, l0);
       }
     }
     __syncthreads();
@@ -125,7 +124,12 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
 #pragma unroll
   for (int m = 0; m < MAXP; ++m) {
     int p = t + m * DTHREADS;
-    if (p < npairs) out[p] = acc[m];
+    if (p < npairs) {
+      df_merge(ah[m][0], al[m][0], ah[m][1], al[m][1]);
+      df_merge(ah[m][2], al[m][2], ah[m][3], al[m][3]);
+      df_merge(ah[m][0], al[m][0], ah[m][2], al[m][2]);
+      out[p] = df_value(ah[m][0], al[m][0]);
+    }
   }
 }
 
@@ -177,7 +181,8 @@ __device__ double block_sum_d(double v, double* red) {
 }
 
 constexpr int PINV_FAST_R = 64;
-constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / DTHREADS;   // entries per thread
+constexpr int PINV_THREADS = 1024;
+constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / PINV_THREADS;   // entries per thread
 
 // Fast path for R <= 64 on the float32 pipes: Gauss-Jordan in float32 gives
 // X0 ~ G^{-1}; Newton-Schulz steps X <- X + X (I - G X) with G X formed in
@@ -187,7 +192,7 @@ constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / DTHREADS;   // entries pe
 // 1e-10 within 6 steps; the float64 path then decides.
 __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
   __shared__ float rowk[PINV_FAST_R], colk[PINV_FAST_R];
-  __shared__ float red[DTHREADS / 32];
+  __shared__ float red[PINV_THREADS / 32];
   const int t = threadIdx.x;
   const int RR = R * R;
   float* Gh = sm;
@@ -195,7 +200,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
   float* Xh = Gl + RR;
   float* Xl = Xh + RR;
   float* W = Xl + RR;
-  for (int e = t; e < RR; e += DTHREADS) {
+  for (int e = t; e < RR; e += PINV_THREADS) {
     double v = 1.0;
     for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
     if (jb.out_had) jb.out_had[e] = v;
@@ -213,7 +218,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
     const float piv = rowk[k];
     if (!(piv > 1e-6f * maxd) || !isfinite(piv)) return false;    // uniform
     const float inv = 1.0f / piv;
-    for (int e = t; e < RR; e += DTHREADS) {
+    for (int e = t; e < RR; e += PINV_THREADS) {
       const int i = e / R, j = e % R;
       float v;
       if (i == k) v = (j == k) ? inv : rowk[j] * inv;
@@ -223,13 +228,13 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
     }
     __syncthreads();
   }
-  for (int e = t; e < RR; e += DTHREADS) { Xh[e] = W[e]; Xl[e] = 0.0f; }
+  for (int e = t; e < RR; e += PINV_THREADS) { Xh[e] = W[e]; Xl[e] = 0.0f; }
   __syncthreads();
   bool ok = false;
   for (int it = 0; it < 6 && !ok; ++it) {
     // W = I - G X with G X in df64
     float emax = 0.0f;
-    for (int e = t; e < RR; e += DTHREADS) {
+    for (int e = t; e < RR; e += PINV_THREADS) {
       const int i = e / R, j = e % R;
       float ah = 0.0f, al = 0.0f;
       for (int k = 0; k < R; ++k) {
@@ -249,14 +254,14 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
     if ((t & 31) == 0) red[t >> 5] = emax;
     __syncthreads();
     float em = 0.0f;
-    for (int w = 0; w < DTHREADS / 32; ++w) em = fmaxf(em, red[w]);
+    for (int w = 0; w < PINV_THREADS / 32; ++w) em = fmaxf(em, red[w]);
     if (!isfinite(em)) return false;
     // X <- X + X W (the correction is small: float32 suffices); once the
     // residual is below 1e-10 this last step leaves X at the df64 noise level
     float corr[PINV_PER_T];
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
-      const int e = t + m * DTHREADS;
+      const int e = t + m * PINV_THREADS;
       float c = 0.0f;
       if (e < RR) {
         const int i = e / R, j = e % R;
@@ -267,7 +272,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
-      const int e = t + m * DTHREADS;
+      const int e = t + m * PINV_THREADS;
       if (e < RR) {
         float sh, se;
         df_two_sum(Xh[e], corr[m], sh, se);
@@ -279,7 +284,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
     ok = em < 1e-10f;
   }
   if (!ok) return false;
-  for (int e = t; e < RR; e += DTHREADS) {
+  for (int e = t; e < RR; e += PINV_THREADS) {
     const int i = e / R, j = e % R;
     jb.out_pinv[e] = 0.5 * (df_value(Xh[e], Xl[e]) + df_value(Xh[j * R + i], Xl[j * R + i]));
   }
@@ -292,7 +297,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
 // Jacobi eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped.
 // One block; each elimination step copies row and column k aside, then every
 // thread updates its entries (two barriers per step, no serial thread).
-__global__ void __launch_bounds__(DTHREADS) pinv_kernel(PinvJobs jobs, int R) {
+__global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R) {
   extern __shared__ double A[];                     // R x R
   __shared__ double red[40];
   __shared__ int sp[64], sq[64];
@@ -447,6 +452,9 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
   for (int c = lane; c < CPD_MAX_RANK; c += 32) wsq[wid][c] = 0.0;
   __syncthreads();
   const int c0 = q * CPT;
+  float csq[CPT];
+#pragma unroll
+  for (int cc = 0; cc < CPT; ++cc) csq[cc] = 0.0f;
   for (int64_t r0 = (int64_t)blockIdx.x * (DTHREADS / 4); r0 < I; r0 += (int64_t)gridDim.x * (DTHREADS / 4)) {
     const int64_t i = r0 + rl;
     const bool live = i < I;
@@ -483,13 +491,17 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
         if (c0 + 4 * v < Rp) urow[v] = make_float4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
     }
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) {
-      float sq = live ? out[cc] * out[cc] : 0.0f;
-      sq += __shfl_xor_sync(CPD_FULL, sq, 4);
-      sq += __shfl_xor_sync(CPD_FULL, sq, 8);
-      sq += __shfl_xor_sync(CPD_FULL, sq, 16);
-      if (lane < 4 && c0 + cc < R) wsq[wid][c0 + cc] += (double)sq;
-    }
+    for (int cc = 0; cc < CPT; ++cc)
+      if (live) csq[cc] = fmaf(out[cc], out[cc], csq[cc]);
+  }
+  // (float32 suffices: a thread holds a few rows; float64 only per block)
+#pragma unroll
+  for (int cc = 0; cc < CPT; ++cc) {
+    float sq = csq[cc];
+    sq += __shfl_xor_sync(CPD_FULL, sq, 4);
+    sq += __shfl_xor_sync(CPD_FULL, sq, 8);
+    sq += __shfl_xor_sync(CPD_FULL, sq, 16);
+    if (lane < 4 && c0 + cc < R) wsq[wid][c0 + cc] = (double)sq;
   }
   __syncthreads();
   for (int c = t; c < R; c += DTHREADS) {
@@ -627,7 +639,7 @@ static cpd_status launch_pinv(cpd_ctx* h, const PinvJobs& jobs, int njobs) {
   PhaseTimer pt(h, CPD_PHASE_PINV);
   const int R = h->R;
   size_t shm = pinv_smem(R);
-  pinv_kernel<<<njobs, DTHREADS, shm, h->stream>>>(jobs, R);
+  pinv_kernel<<<njobs, PINV_THREADS, shm, h->stream>>>(jobs, R);
   CPD_LAUNCH(h, "pinv");
   return CPD_OK;
 }

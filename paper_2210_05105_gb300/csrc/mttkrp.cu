@@ -1,14 +1,13 @@
 // Downsampled MTTKRP  Y = mat(T, n) S^T S U_{!=n}  (Eq. 7, Fig. 2 bottom) and
 // the exact MTTKRP of Eq. 6.
 //
-// Sampled path, three launches after clearing Y and the per-call tables:
-//  1. probe  (one warp per draw): KRP-row key of the draw, hash lookup of its
+// Sampled path, two launches after clearing Y and the per-call tables:
+//  1. probe  (one lane per draw): KRP-row key of the draw, hash lookup of its
 //     nonzero range in the mode layout, merge with earlier draws of the same
-//     column (their weights add: S^T S is diagonal over KRP rows), and for
-//     the first draw of a column the KRP row h = *_{k != n} U_k[i_k, :];
-//  2. scan   (one block): offsets of each distinct column's nonzeros in the
-//     flat list of selected nonzeros, total nnz(mat(T, n) S^T);
-//  3. spmm   (persistent grid): warps take 32 consecutive selected nonzeros
+//     column (their weights add: S^T S is diagonal over KRP rows); the first
+//     draw of a column reserves its place in the flat list of selected
+//     nonzeros and writes the KRP row h = *_{k != n} U_k[i_k, :];
+//  2. spmm   (persistent grid): warps take 32 consecutive selected nonzeros
 //     (load balanced regardless of column lengths) and add
 //     w_col * val * h_col into row i_n of Y.
 #include "common.cuh"
@@ -26,10 +25,10 @@ struct MArgs {
   unsigned long long mask;
   const uint2* ent;
   uint32_t* dd_tag;
-  double* dd_w;
+  float* dd_w;
   uint32_t dmask;
   uint32_t* uq_slot;
-  uint32_t* uq_len;
+  uint32_t* chunk_seg;
   uint32_t* uq_off;
   float* H;
   uint32_t* counters;
@@ -53,101 +52,83 @@ __device__ __forceinline__ bool fiber_lookup(const FiberSlot* __restrict__ table
   return false;
 }
 
+// One lane per draw: KRP-row key, hash lookup of the column's nonzero range,
+// merge with earlier draws of the same column (weights add: S^T S is
+// diagonal over KRP rows).  The first draw of a column takes, with one 64-bit
+// atomic, both its index u among the distinct columns and the offset of its
+// nonzeros in the flat list of selected nonzeros (so no separate scan).  The
+// warp then writes the KRP row h_u = *_{k != n} U_k[i_k, :] of each such
+// column and marks the 32-nonzero chunks that start inside its range.
 __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const double* __restrict__ w, int64_t J) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool mine = lane < a.N && lane != a.n;
-  for (int64_t j = warp; j < J; j += nwarps) {
-    int32_t ik = mine ? idx[(int64_t)lane * J + j] : 0;
-    bool bad = mine && (ik < 0 || (int64_t)ik >= a.dims[lane]);
-    if (__any_sync(CPD_FULL, bad)) {
-      if (lane == 0) cpd_set_status(a.status, CPD_ERR_OUT_OF_RANGE_INDEX);
-      continue;
-    }
-    unsigned long long key = mine ? (unsigned long long)ik * a.stride[lane] : 0ull;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(a.counters);
+  for (int64_t j0 = warp * 32; j0 < J; j0 += nwarps * 32) {
+    const int64_t j = j0 + lane;
+    const bool valid = j < J;
+    int32_t ik[CPD_MAX_MODES];
+    unsigned long long key = 0;
+    bool bad = false;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) key += __shfl_xor_sync(CPD_FULL, key, o);   // lanes 0..7 hold the modes
-    key = __shfl_sync(CPD_FULL, key, 0);
-    uint32_t beg = 0, len = 0, u = 0;
-    int won = 0, found = 0;
-    if (lane == 0) {
-      found = fiber_lookup(a.table, a.mask, key, beg, len);
-      if (found) {
-        uint32_t s = (uint32_t)cpd_mix64((unsigned long long)beg) & a.dmask;
-        for (uint32_t probe = 0; probe <= a.dmask; ++probe) {
-          uint32_t old = atomicCAS(&a.dd_tag[s], CPD_EMPTY32, beg);
-          if (old == CPD_EMPTY32) { won = 1; break; }
-          if (old == beg) break;
-          s = (s + 1) & a.dmask;
-        }
-        atomicAdd(&a.dd_w[s], w[j]);
-        if (won) {
-          u = atomicAdd(&a.counters[0], 1u);
-          if (u < a.uq_cap) { a.uq_slot[u] = s; a.uq_len[u] = len; }
-          else { cpd_set_status(a.status, CPD_ERR_CAPACITY); won = 0; }
-        }
+    for (int k = 0; k < CPD_MAX_MODES; ++k) {
+      ik[k] = 0;
+      if (k < a.N && k != a.n && valid) {
+        ik[k] = idx[(int64_t)k * J + j];
+        if (ik[k] < 0 || (int64_t)ik[k] >= a.dims[k]) bad = true;
+        key += (unsigned long long)(bad ? 0 : ik[k]) * a.stride[k];
       }
     }
-    won = __shfl_sync(CPD_FULL, won, 0);
-    if (!won) continue;
-    u = __shfl_sync(CPD_FULL, u, 0);
-    for (int r = lane; r < a.Rp; r += 32) {
-      float v = r < a.R ? 1.0f : 0.0f;
-      for (int k = 0; k < a.N; ++k) {
-        int32_t ikk = __shfl_sync(CPD_FULL, ik, k);
-        if (k != a.n && r < a.R) v *= a.U[k][(int64_t)ikk * a.Rp + r];
+    if (bad) cpd_set_status(a.status, CPD_ERR_OUT_OF_RANGE_INDEX);
+    uint32_t beg = 0, len = 0, u = 0, off = 0;
+    bool won = false;
+    if (valid && !bad && fiber_lookup(a.table, a.mask, key, beg, len)) {
+      uint32_t sl = (uint32_t)cpd_mix64((unsigned long long)beg) & a.dmask;
+      for (uint32_t probe = 0; probe <= a.dmask; ++probe) {
+        const uint32_t old = atomicCAS(&a.dd_tag[sl], CPD_EMPTY32, beg);
+        if (old == CPD_EMPTY32) { won = true; break; }
+        if (old == beg) break;
+        sl = (sl + 1) & a.dmask;
       }
-      a.H[(int64_t)u * a.Rp + r] = v;
+      atomicAdd(&a.dd_w[sl], (float)w[j]);
+      if (won) {
+        const unsigned long long pk = atomicAdd(ctr, (1ull << 32) | (unsigned long long)len);
+        u = (uint32_t)(pk >> 32);
+        off = (uint32_t)(pk & 0xffffffffull);
+        if (u < a.uq_cap) { a.uq_slot[u] = sl; a.uq_off[u] = off; }
+        else { cpd_set_status(a.status, CPD_ERR_CAPACITY); won = false; }
+      }
+    }
+    for (unsigned m = __ballot_sync(CPD_FULL, won); m; m &= m - 1) {
+      const int b = __ffs(m) - 1;
+      const uint32_t ub = __shfl_sync(CPD_FULL, u, b);
+      const uint32_t ob = __shfl_sync(CPD_FULL, off, b);
+      const uint32_t lb = __shfl_sync(CPD_FULL, len, b);
+      int32_t ib[CPD_MAX_MODES];
+#pragma unroll
+      for (int k = 0; k < CPD_MAX_MODES; ++k) ib[k] = __shfl_sync(CPD_FULL, ik[k], b);
+      for (int r = lane; r < a.Rp; r += 32) {
+        float v = r < a.R ? 1.0f : 0.0f;
+#pragma unroll
+        for (int k = 0; k < CPD_MAX_MODES; ++k)
+          if (k < a.N && k != a.n && r < a.R) v *= a.U[k][(int64_t)ib[k] * a.Rp + r];
+        a.H[(int64_t)ub * a.Rp + r] = v;
+      }
+      // chunks c whose first position 32 c lies in [ob, ob + lb)
+      const uint32_t c1 = (ob + 31) >> 5, c2 = (ob + lb - 1) >> 5;
+      for (uint32_t c = c1 + lane; c <= c2; c += 32) a.chunk_seg[c] = ub;
     }
   }
 }
 
-// One block: exclusive offsets of the distinct columns' nonzero counts.
-__global__ void __launch_bounds__(1024) scan_kernel(MArgs a, int64_t* __restrict__ out_nnz_sel) {
-  __shared__ uint32_t wsum[32];
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const uint32_t nu = min(a.counters[0], a.uq_cap);
-  const uint32_t per = (nu + 1023) / 1024;
-  const uint32_t b0 = t * per;
-  uint32_t s = 0;
-  for (uint32_t q = 0; q < per; ++q)
-    if (b0 + q < nu) s += a.uq_len[b0 + q];
-  uint32_t x = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(CPD_FULL, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t v = wsum[lane];
-    uint32_t z = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(CPD_FULL, z, o);
-      if (lane >= o) z += y;
-    }
-    wsum[lane] = z - v;
-  }
-  __syncthreads();
-  uint32_t run = wsum[wid] + x - s;
-  for (uint32_t q = 0; q < per; ++q)
-    if (b0 + q < nu) { uint32_t v = a.uq_len[b0 + q]; a.uq_off[b0 + q] = run; run += v; }
-  if (t == 1023) {
-    a.uq_off[nu] = run;
-    a.counters[1] = run;
-    if (out_nnz_sel) *out_nnz_sel = (int64_t)run;
-  }
-}
-
-__global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ Y) {
+__global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const uint32_t nu = min(a.counters[0], a.uq_cap);
-  const uint32_t total = a.counters[1];
+  const unsigned long long pk = *reinterpret_cast<const unsigned long long*>(a.counters);
+  const uint32_t nu = min((uint32_t)(pk >> 32), a.uq_cap);
+  const uint32_t total = (uint32_t)(pk & 0xffffffffull);
+  if (out_nnz_sel && blockIdx.x == 0 && threadIdx.x == 0) *out_nnz_sel = (int64_t)total;
   const int64_t nchunks = ((int64_t)total + 31) / 32;
   const int C = a.Rp / 4;                 // float4 chunks per row
   const int E = C >= 32 ? 1 : 32 / C;     // nonzeros per warp instruction
@@ -155,20 +136,11 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
   const int q = C >= 32 ? lane : lane % C;
   for (int64_t c = warp; c < nchunks; c += nwarps) {
     const int64_t p = c * 32 + lane;
-    // The 32 positions of the chunk meet at most 32 consecutive segments:
-    // one search finds the first, the window of their offsets goes to the
-    // lanes, and each lane locates its own segment in the window by shuffles.
-    uint32_t seg0 = 0;
-    if (lane == 0) {
-      uint32_t lo = 0, hi = nu - 1;        // last segment with offset <= c * 32
-      const uint32_t p0 = (uint32_t)(c * 32);
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (a.uq_off[mid] <= p0) lo = mid; else hi = mid - 1;
-      }
-      seg0 = lo;
-    }
-    seg0 = __shfl_sync(CPD_FULL, seg0, 0);
+    // The 32 positions of the chunk meet at most 32 consecutive segments
+    // starting at the one the probe recorded for the chunk; the window of
+    // their offsets goes to the lanes, and each lane locates its own segment
+    // in the window by shuffles.
+    const uint32_t seg0 = a.chunk_seg[c];
     const uint32_t wseg = seg0 + lane;
     const uint32_t woff = wseg < nu ? a.uq_off[wseg] : 0xffffffffu;
     uint32_t loc = 0;                      // last window slot with offset <= p
@@ -186,7 +158,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
       const uint32_t e = a.dd_tag[slot] + ((uint32_t)p - segoff);
       const uint2 en = a.ent[e];
       row = en.x;
-      scale = (float)(a.dd_w[slot] * (double)__uint_as_float(en.y));
+      scale = a.dd_w[slot] * __uint_as_float(en.y);
     }
     const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
     // C lanes cover one row of Rp floats with 16-byte vector reductions, so
@@ -238,6 +210,30 @@ __global__ void exact_kernel(MArgs a, const int32_t* __restrict__ idx, const flo
   }
 }
 
+// Rows of the downsampled design matrix S U_{!=n}: sqrt(w_j) h_j, one warp
+// per draw (their Gram is the sketched Gram of Fig. 2, bottom).
+__global__ void sketch_rows_kernel(MArgs a, const int32_t* __restrict__ idx, const double* __restrict__ w, int64_t J,
+                                   float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < J; j += nwarps) {
+    const bool mine = lane < a.N && lane != a.n;
+    int32_t ik = mine ? idx[(int64_t)lane * J + j] : 0;
+    const bool bad = mine && (ik < 0 || (int64_t)ik >= a.dims[lane]);
+    const bool any_bad = __any_sync(CPD_FULL, bad);
+    const float sw = (float)sqrt(fmax(w[j], 0.0));
+    for (int r = lane; r < a.Rp; r += 32) {
+      float v = (r < a.R && !any_bad) ? sw : 0.0f;
+      for (int k = 0; k < a.N; ++k) {
+        const int32_t ikk = __shfl_sync(CPD_FULL, ik, k);
+        if (k != a.n && r < a.R && !any_bad) v *= a.U[k][(int64_t)ikk * a.Rp + r];
+      }
+      out[j * a.Rp + r] = v;
+    }
+  }
+}
+
 MArgs make_args(cpd_ctx* h, int mode) {
   MArgs a;
   memset(&a, 0, sizeof(a));
@@ -251,7 +247,7 @@ MArgs make_args(cpd_ctx* h, int mode) {
   a.mask = h->mode[mode].mask;
   a.ent = h->mode[mode].ent;
   a.dd_tag = h->dd_tag; a.dd_w = h->dd_w; a.dmask = h->dedup_mask;
-  a.uq_slot = h->uq_slot; a.uq_len = h->uq_len; a.uq_off = h->uq_off;
+  a.uq_slot = h->uq_slot; a.chunk_seg = h->chunk_seg; a.uq_off = h->uq_off;
   a.H = h->H; a.counters = h->counters; a.status = h->status;
   a.uq_cap = (uint32_t)h->Jcap;
   return a;
@@ -268,27 +264,35 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
     PhaseTimer pt(h, CPD_PHASE_CLEAR);
     CPD_CUDA(h, cudaMemsetAsync(Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), st));
     CPD_CUDA(h, cudaMemsetAsync(h->dd_tag, 0xff, ((size_t)h->dedup_mask + 1) * sizeof(uint32_t), st));
-    CPD_CUDA(h, cudaMemsetAsync(h->dd_w, 0, ((size_t)h->dedup_mask + 1) * sizeof(double), st));
+    CPD_CUDA(h, cudaMemsetAsync(h->dd_w, 0, ((size_t)h->dedup_mask + 1) * sizeof(float), st));
     CPD_CUDA(h, cudaMemsetAsync(h->counters, 0, 4 * sizeof(uint32_t), st));
   }
   MArgs a = make_args(h, mode);
   if (J > 0) {
     PhaseTimer pt(h, CPD_PHASE_PROBE);
-    int grid = (int)std::min<int64_t>(cpd_ceil_div(J * 32, 256), (int64_t)h->num_sms * 16);
+    int grid = (int)std::min<int64_t>(cpd_ceil_div(J, 256), (int64_t)h->num_sms * 16);
     probe_kernel<<<grid, 256, 0, st>>>(a, idx, w, J);
     CPD_LAUNCH(h, "probe");
   }
   {
-    PhaseTimer pt(h, CPD_PHASE_SCAN);
-    scan_kernel<<<1, 1024, 0, st>>>(a, out_nnz_sel);
-    CPD_LAUNCH(h, "scan");
-  }
-  {
     PhaseTimer pt(h, CPD_PHASE_SPMM);
-    spmm_kernel<<<h->num_sms * 8, 256, 0, st>>>(a, Y);
+    spmm_kernel<<<h->num_sms * 8, 256, 0, st>>>(a, Y, out_nnz_sel);
     CPD_LAUNCH(h, "spmm");
   }
+  if (h->opt.sketched_gram) return cpd_sketch_gram(h, mode, idx, w, J);
   return CPD_OK;
+}
+
+// Sketched Gram sum_j w_j h_j h_j^T of a draw list into h->Gsk (uses h->H as
+// scratch, after the SpMM has consumed it).
+cpd_status cpd_sketch_gram(cpd_ctx* h, int mode, const int32_t* idx, const double* w, int64_t J) {
+  MArgs a = make_args(h, mode);
+  if (J > 0) {
+    int grid = (int)std::min<int64_t>(cpd_ceil_div(J * 32, 256), (int64_t)h->num_sms * 16);
+    sketch_rows_kernel<<<grid, 256, 0, h->stream>>>(a, idx, w, J, h->H);
+    CPD_LAUNCH(h, "sketch_rows");
+  }
+  return cpd_gram(h, h->H, J, h->Gsk);
 }
 
 cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y) {

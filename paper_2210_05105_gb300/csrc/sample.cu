@@ -140,10 +140,14 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
       const double C = cdf[I - 1];
       const double t = cpd_uniform(a.seed, CPD_STREAM_ARLS, (unsigned long long)j, (unsigned long long)k,
                                    (unsigned long long)a.n, s) * C;
-      int64_t lo = 0, hi = I;           // first index in [lo, hi) with cdf > t
+      // first index in [lo, hi) with cdf > t; non-negative doubles order as
+      // their bit patterns, so the search compares integers (no FP64 pipe)
+      const long long tb = __double_as_longlong(t);
+      const long long* cb = reinterpret_cast<const long long*>(cdf);
+      int64_t lo = 0, hi = I;
       while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
-        if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+        if (cb[mid] > tb) hi = mid; else lo = mid + 1;
       }
       if (lo >= I) {
         lo = I - 1;

@@ -273,10 +273,12 @@ __global__ void sts_first_kernel(const double* __restrict__ cdf, const double* _
     const double C = cdf[I - 1];
     const double t = cpd_uniform(seed, CPD_STREAM_STS, (unsigned long long)j, (unsigned long long)k,
                                  (unsigned long long)n, s) * C;
+    const long long tb = __double_as_longlong(t);         // non-negative: bit order = value order
+    const long long* cb = reinterpret_cast<const long long*>(cdf);
     int64_t lo = 0, hi = I;
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+      if (cb[mid] > tb) hi = mid; else lo = mid + 1;
     }
     if (lo >= I) {
       lo = I - 1;

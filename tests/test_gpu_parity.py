@@ -270,3 +270,37 @@ def test_invalid_inputs_are_reported(cpd):
     # the handle stays usable afterwards
     Y, _ = cpd.cpd_sampled_mttkrp(h, 0, torch.zeros((3, 4), dtype=torch.int32), torch.ones(4, dtype=torch.float64))
     h.close()
+
+
+def test_sketched_gram_solve_matches_oracle(cpd):
+    """options.sketched_gram = 1: U_n = Y G~^+ with G~ the Gram of the draws
+    (Fig. 2, bottom), step by step against the oracle."""
+    dims, R, J = SMALL["dims"], SMALL["R"], SMALL["J"]
+    idx, vals, init = make_case(dims, SMALL["nnz"], R, seed=1001)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=3001,
+                       sketched_gram=True)
+    for n in range(3):
+        fs = gpu_factors(cpd, h)
+        gi, gp = cpd.cpd_leverage_sample(h, n, J, 0)
+        w = 1.0 / (J * gp)
+        Y, _ = cpd.cpd_sampled_mttkrp(h, n, gi, w)
+        cpd.cpd_gram_solve(h, n, Y)
+        Gsk = oc.sketched_gram(fs, n, gi.cpu().numpy(), w.cpu().numpy())
+        Uo, _ = oc.solve_and_renorm(Y.double().cpu().numpy(), oc.pinv_sym(Gsk))
+        assert rel_frob(cpd.cpd_get_factors(h, n).double().cpu().numpy(), Uo) < 1e-5
+    h.close()
+
+
+def test_sketched_gram_end_to_end_fit(cpd):
+    dims, R, J = SMALL["dims"], SMALL["R"], SMALL["J"]
+    idx, vals, init = make_case(dims, SMALL["nnz"], R, seed=1001)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=3001,
+                       sketched_gram=True)
+    cpd.cpd_als_sweep(h, 5)
+    f_gpu = cpd.cpd_fit(h)
+    _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], "arls", 5, J=J, seed=3001,
+                     sketched=True)
+    assert abs(f_gpu - fits[-1]) < 1e-3
+    h.close()

@@ -330,3 +330,31 @@ def test_sampled_update_is_unbiased():
     sd = np.sqrt(np.maximum(acc2 / trials - mean ** 2, 0) / trials)
     exact = oc.exact_mttkrp(idx, vals, dims, fs, n)
     assert np.all(np.abs(mean - exact) <= 5 * sd + 1e-9)
+
+
+def test_sketched_gram_matches_explicit_sampling_matrix():
+    rng = np.random.default_rng(30)
+    dims = (5, 4, 6)
+    fs = [rng.standard_normal((d, 3)) for d in dims]
+    for n in range(3):
+        J = 23
+        sidx = np.stack([rng.integers(0, d, J) for d in dims])
+        sidx[n] = -1
+        w = rng.random(J) + 0.2
+        A = khatri_rao_design(fs, n)
+        ncols = A.shape[0]
+        S = np.zeros((J, ncols))
+        S[np.arange(J), oc.krp_key(sidx, dims, n)] = np.sqrt(w)
+        assert np.allclose(oc.sketched_gram(fs, n, sidx, w), (S @ A).T @ (S @ A))
+
+
+def test_sketched_gram_als_solves_consistent_problems_exactly():
+    """With the downsampled normal equations (Fig. 2, bottom) an exactly
+    rank-R tensor is a consistent least-squares problem: every full-rank
+    sketch recovers the exact update, so the fit reaches 1 (no J^-1/2 floor,
+    unlike the unbiased exact-G^+ update)."""
+    dims = (9, 8, 7)
+    idx, vals, _ = planted_dense(dims, 3, 31)
+    init = synth.init_factors(dims, 3, 42)
+    _, fits = oc.als(idx, vals, dims, init, "arls", 60, J=200, seed=5, sketched=True)
+    assert fits[-1] > 0.9999
