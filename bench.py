@@ -46,7 +46,11 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--method", default="arls", choices=["arls", "sts"])
+    p.add_argument("--method", default="arls", choices=["arls", "sts", "exact"])
+    p.add_argument("--sketched", action="store_true", help="solve with the Gram of the draws (Fig. 2, bottom)")
+    p.add_argument("--samples", type=int, default=0, help="override J of the workload")
+    p.add_argument("--study-J", default="", help="comma-separated J values: print one line per J (runtime breakdown "
+                   "and fit after --steps sweeps), the sample-count study of the paper's Figs. 11-12")
     p.add_argument("--workload", default="zipf_1e5cube_50M", choices=sorted(synth.WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -190,17 +194,70 @@ def algorithmic(phase, w, stats):
     if phase == "solve":
         I = stats["I_mean"]
         return "hbm", I * Rp * 4 * 2
+    if phase == "exact":
+        # every nonzero: N indices + value, N - 1 factor rows, one output row update
+        nnz = w["nnz"]
+        return "hbm", nnz * (N * 4 + 4) + nnz * (N - 1) * R * 4 + stats["I_mean"] * R * 4
     return "hbm", 0
+
+
+def workload(args):
+    w = dict(synth.WORKLOADS[args.workload])
+    if args.samples:
+        w["J"] = args.samples
+    return w
+
+
+def study_J(args):
+    """Runtime breakdown and fit against the sample count J (Figs. 11-12)."""
+    import torch
+    from paper_2210_05105_gb300 import cpd
+    w = workload(args)
+    dims, R = w["dims"], w["R"]
+    N = len(dims)
+    idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
+    init = [torch.from_numpy(u).cuda() for u in synth.init_factors(dims, R, w["init_seed"])]
+    for J in [int(x) for x in args.study_J.split(",")]:
+        h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
+                           sketched_gram=args.sketched)
+        cpd.cpd_als_sweep(h, args.warmup)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        cpd.cpd_als_sweep(h, args.steps, sync=False)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        fit = cpd.cpd_fit(h)
+        cpd.cpd_profile(h, True)
+        nsel = 0
+        for n in range(N):
+            gi, gp = cpd.cpd_leverage_sample(h, n, J, args.warmup + args.steps)
+            Y, ns = cpd.cpd_sampled_mttkrp(h, n, gi, 1.0 / (J * gp))
+            nsel += ns
+            cpd.cpd_gram_solve(h, n, Y)
+        ph = cpd.cpd_profile_read(h)
+        h.close()
+        groups = {"sampling": ["draw", "pinv"], "mttkrp": ["clear", "probe", "scan", "spmm"],
+                  "post-processing": ["solve", "gram", "sampler"]}
+        print(json.dumps({"study": "sample count", "workload": args.workload, "method": args.method,
+                          "sketched_gram": args.sketched, "J": J, "ms_per_sweep": ms,
+                          "fit_after_%d_sweeps" % (args.warmup + args.steps): fit,
+                          "nnz_sel_per_mode": nsel / N,
+                          "phase_ms_per_sweep": {g: round(sum(ph[k][0] for k in ks), 4) for g, ks in groups.items()}}))
 
 
 def ours(args, world, rank, local):
     import torch
     from paper_2210_05105_gb300 import cpd
     torch.cuda.set_device(local)
+    if args.study_J:
+        study_J(args)
+        return
     if world > 1:
         import torch.distributed as tdist
         tdist.init_process_group("nccl")
-    w = synth.WORKLOADS[args.workload]
+    w = workload(args)
     dims, R, J = w["dims"], w["R"], w["J"]
     N = len(dims)
     idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
@@ -208,7 +265,8 @@ def ours(args, world, rank, local):
     init = [torch.from_numpy(u).cuda() for u in init_np]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"])
+    h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
+                       sketched_gram=args.sketched)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
 
@@ -242,6 +300,11 @@ def ours(args, world, rank, local):
     stats = {"nnz_sel": 0, "J_u": 0, "rows": 0, "I_mean": sum(dims) / N}
     spmm_ms_list = []
     for n in range(N):
+        if args.method == "exact":
+            Y = cpd.cpd_exact_mttkrp(h, n)
+            cpd.cpd_gram_solve(h, n, Y)
+            stats.setdefault("phases", []).append(cpd.cpd_profile_read(h))
+            continue
         gi, gp = cpd.cpd_leverage_sample(h, n, J, sweep_id)
         wts = 1.0 / (J * gp)
         before = cpd.cpd_profile_read(h)
@@ -287,8 +350,8 @@ def ours(args, world, rank, local):
         return {"phase": phase, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind}
 
-    roofline = roof(dominant)
-    roofline_spmm = roof("spmm")
+    roofline = roof("exact" if args.method == "exact" else "spmm")
+    roofline_spmm = roofline
 
     # end-to-end through the C ABI from pinned host buffers
     e2e = None
@@ -298,7 +361,8 @@ def ours(args, world, rank, local):
         init_h = [u.cpu().pin_memory() for u in init]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2 = cpd.cpd_create(dims, idx_h, vals_h, init_h, method=args.method, rank=R, samples=J, seed=w["sample_seed"])
+        h2 = cpd.cpd_create(dims, idx_h, vals_h, init_h, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
+                            sketched_gram=args.sketched)
         cpd.cpd_als_sweep(h2, args.steps, sync=False)
         f2 = cpd.cpd_fit(h2)
         outs = [cpd.cpd_get_factors(h2, k, out=torch.empty((dims[k], R), dtype=torch.float32).pin_memory())

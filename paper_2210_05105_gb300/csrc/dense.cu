@@ -44,14 +44,19 @@ __global__ void colsq_kernel(const float* __restrict__ U, int64_t I, int R, int 
   store_col_partials(g < groups ? acc : 0.0, R, groups, part + (int64_t)blockIdx.x * R);
 }
 
-// sigma_r = sqrt(sum of partials): one warp per column, fixed order.
+// sigma_r = sqrt(sum of partials): one block per column, fixed order.
 __global__ void sigma_kernel(const double* __restrict__ part, int nblk, int R, double* __restrict__ sigma) {
-  const int lane = threadIdx.x & 31;
-  for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
-    double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * R + r];
-    s = warp_sum(s);
-    if (lane == 0) sigma[r] = sqrt(s);
+  __shared__ double red[32];
+  const int r = blockIdx.x, t = threadIdx.x;
+  double s = 0.0;
+  for (int b = t; b < nblk; b += blockDim.x) s += part[(int64_t)b * R + r];
+  s = warp_sum(s);
+  if ((t & 31) == 0) red[t >> 5] = s;
+  __syncthreads();
+  if (t == 0) {
+    double z = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) z += red[w];
+    sigma[r] = sqrt(z);
   }
 }
 
@@ -621,7 +626,7 @@ cpd_status cpd_renormalize_inputs(cpd_ctx* h) {
   const int R = h->R;
   for (int k = 0; k < h->N; ++k) {
     colsq_kernel<<<h->gram_blocks, DTHREADS, 0, h->stream>>>(h->U[k], h->dims[k], R, h->Rp, h->colsq);
-    sigma_kernel<<<1, 1024, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
+    sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
     CPD_LAUNCH(h, "colsq/sigma");
     cpd_status s = gram_from(h, h->U[k], h->U[k], h->dims[k], h->sigma, 1, h->G[k]);
     if (s != CPD_OK) return s;
@@ -684,7 +689,7 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     else
       solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
     CPD_LAUNCH(h, "solve");
-    sigma_kernel<<<1, 1024, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
+    sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
     CPD_LAUNCH(h, "sigma");
   }
   if (out_sigma && out_sigma != h->sigma)

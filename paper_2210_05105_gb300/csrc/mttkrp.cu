@@ -99,24 +99,24 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
         else { cpd_set_status(a.status, CPD_ERR_CAPACITY); won = false; }
       }
     }
-    for (unsigned m = __ballot_sync(CPD_FULL, won); m; m &= m - 1) {
-      const int b = __ffs(m) - 1;
-      const uint32_t ub = __shfl_sync(CPD_FULL, u, b);
-      const uint32_t ob = __shfl_sync(CPD_FULL, off, b);
-      const uint32_t lb = __shfl_sync(CPD_FULL, len, b);
-      int32_t ib[CPD_MAX_MODES];
+    if (won) {
+      // the winning lane writes its column's KRP row (16-byte vectors; rows
+      // are independent, so the lanes' gathers overlap) ...
+      float4* hrow = reinterpret_cast<float4*>(a.H + (int64_t)u * a.Rp);
+      for (int v4 = 0; v4 < a.Rp / 4; ++v4) {
+        float4 x = make_float4(1.f, 1.f, 1.f, 1.f);
 #pragma unroll
-      for (int k = 0; k < CPD_MAX_MODES; ++k) ib[k] = __shfl_sync(CPD_FULL, ik[k], b);
-      for (int r = lane; r < a.Rp; r += 32) {
-        float v = r < a.R ? 1.0f : 0.0f;
-#pragma unroll
-        for (int k = 0; k < CPD_MAX_MODES; ++k)
-          if (k < a.N && k != a.n && r < a.R) v *= a.U[k][(int64_t)ib[k] * a.Rp + r];
-        a.H[(int64_t)ub * a.Rp + r] = v;
+        for (int k = 0; k < CPD_MAX_MODES; ++k) {
+          if (k < a.N && k != a.n) {
+            const float4 f = reinterpret_cast<const float4*>(a.U[k] + (int64_t)ik[k] * a.Rp)[v4];
+            x.x *= f.x; x.y *= f.y; x.z *= f.z; x.w *= f.w;
+          }
+        }
+        hrow[v4] = x;
       }
-      // chunks c whose first position 32 c lies in [ob, ob + lb)
-      const uint32_t c1 = (ob + 31) >> 5, c2 = (ob + lb - 1) >> 5;
-      for (uint32_t c = c1 + lane; c <= c2; c += 32) a.chunk_seg[c] = ub;
+      // ... and marks the chunks c whose first position 32 c lies in its range
+      const uint32_t c1 = (off + 31) >> 5, c2 = (off + len - 1) >> 5;
+      for (uint32_t c = c1; c <= c2; ++c) a.chunk_seg[c] = u;
     }
   }
 }

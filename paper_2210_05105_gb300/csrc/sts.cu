@@ -118,8 +118,21 @@ struct StsArgs {
   int R, Rp, F, D, npairs, k, n, N, first, last;
 };
 
-template <int RB>
+// Group-wide sum over the G lanes of a lane group (G a power of two <= 32).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(CPD_FULL, v, o);
+  return v;
+}
+
+// A warp walks 32 / G draws at once, G lanes per draw: the tree is complete,
+// so every group descends the same number of levels and only the loaded
+// nodes differ, which gives the latency-bound descent 32 / G independent
+// memory streams per warp.
+template <int RB, int G>
 __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
+  constexpr int DPW = 32 / G;                                      // draws per warp
   extern __shared__ float4 sm4[];
   float* Gs = reinterpret_cast<float*>(sm4);                      // R x R
   const int R = a.R, Rp = a.Rp, npairs = a.npairs;
@@ -127,9 +140,10 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
   unsigned char* pa = reinterpret_cast<unsigned char*>(Gs + R * R);
   unsigned char* pb = pa + npad;
   float* wbase = reinterpret_cast<float*>(pb + npad);
-  const int per_warp = npad + Rp + ((a.F + 3) & ~3);
+  const int per_group = npad + Rp + ((a.F + 3) & ~3);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* M = wbase + wid * per_warp;
+  const int grp = lane / G, gl = lane % G;
+  float* M = wbase + (wid * DPW + grp) * per_group;
   float* hs = M + npad;
   float* qb = hs + Rp;
 
@@ -149,38 +163,38 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
   auto mass = [&](int64_t v) -> float {
     const float* g = a.tree + v * npairs;
     float acc = 0.0f;
-    for (int p = lane; p < npairs; p += 32) acc = fmaf(g[p], M[p], acc);
-    return warp_sum(acc);
+    for (int p = gl; p < npairs; p += G) acc = fmaf(g[p], M[p], acc);
+    return group_sum<G>(acc);
   };
 
-  for (int64_t j = warp; j < a.J; j += nwarps) {
-    for (int r = lane; r < Rp; r += 32) hs[r] = a.first ? (r < R ? 1.0f : 0.0f) : a.Hs[j * Rp + r];
+  for (int64_t jb = warp * DPW; jb < a.J; jb += nwarps * DPW) {
+    const int64_t j = jb + grp;
+    const bool live = j < a.J;
+    const int64_t jj = live ? j : a.J - 1;           // dead groups shadow a live draw, write nothing
+    for (int r = gl; r < Rp; r += G) hs[r] = a.Hs[jj * Rp + r];
     __syncwarp();
-    for (int p = lane; p < npairs; p += 32) {
+    for (int p = gl; p < npairs; p += G) {
       const int x = pa[p], y = pb[p];
       M[p] = (x == y ? 1.0f : 2.0f) * Gs[x * R + y] * hs[x] * hs[y];
     }
     __syncwarp();
-    const double u = cpd_uniform(a.seed, CPD_STREAM_STS, (unsigned long long)j, (unsigned long long)a.k,
+    const double u = cpd_uniform(a.seed, CPD_STREAM_STS, (unsigned long long)jj, (unsigned long long)a.k,
                                  (unsigned long long)a.n, s);
     double t = u * (double)mass(1);
     int64_t v = 1;
-    int depth = 0;
-    while (v < a.L) {
+    for (int depth = 0; depth < a.D; ++depth) {
       const int64_t left = 2 * v;
       const float mL = mass(left);
       const int64_t rfirst = (((left + 1) << (a.D - depth - 1)) - a.L) * a.F;
       if (t >= (double)mL && rfirst < a.I) { t -= (double)mL; v = left + 1; }
       else v = left;
-      ++depth;
     }
     const int64_t r0 = (v - a.L) * a.F;
     const int nr = (int)(a.I - r0 < a.F ? a.I - r0 : a.F);
     const float mleaf = mass(v);
-    // row masses of the leaf
+    // row masses of the leaf, rows gl, gl + G, ... of the group
     double qpart = 0.0;
-    for (int c0 = 0; c0 < nr; c0 += 32) {
-      const int i = c0 + lane;
+    for (int i = gl; i < a.F; i += G) {
       float q = 0.0f;
       if (i < nr) {
         const float* urow = a.U + (r0 + i) * Rp;
@@ -202,53 +216,51 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
       qpart += (double)q;
     }
     __syncwarp();
-    const double qs = warp_sum(qpart);
+    const double qs = group_sum<G>(qpart);
     const double tl = mleaf > 0.0f ? t * (qs / (double)mleaf) : 0.0;
     int found = -1;
     double carry = 0.0;
-    for (int c0 = 0; c0 < nr && found < 0; c0 += 32) {
-      const int i = c0 + lane;
-      const double qd = i < nr ? (double)qb[i] : 0.0;
+    const unsigned gmask = (G == 32) ? CPD_FULL : (((1u << G) - 1u) << (grp * G));
+    for (int c0 = 0; c0 < a.F; c0 += G) {
+      const int i = c0 + gl;
+      const double qd = (i < nr) ? (double)qb[i] : 0.0;
       double cum = qd;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        double y = __shfl_up_sync(CPD_FULL, cum, o);
-        if (lane >= o) cum += y;
+      for (int o = 1; o < G; o <<= 1) {
+        const double y = __shfl_up_sync(CPD_FULL, cum, o, G);
+        if (gl >= o) cum += y;
       }
       cum += carry;
-      const unsigned hit = __ballot_sync(CPD_FULL, i < nr && cum > tl);
-      if (hit) found = c0 + __ffs(hit) - 1;
-      carry = __shfl_sync(CPD_FULL, cum, 31);
+      const unsigned hit = __ballot_sync(CPD_FULL, i < nr && cum > tl) & gmask;
+      if (found < 0 && hit) found = c0 + (__ffs(hit) - 1) - grp * G;
+      carry = __shfl_sync(CPD_FULL, cum, G - 1, G);
     }
     if (found < 0) {              // rounding put the target past the end
       found = 0;
-      for (int c0 = 0; c0 < nr; c0 += 32) {
-        const int i = c0 + lane;
-        const unsigned pos = __ballot_sync(CPD_FULL, i < nr && qb[i] > 0.0f);
-        if (pos) found = c0 + 31 - __clz(pos);
+      for (int c0 = 0; c0 < a.F; c0 += G) {
+        const int i = c0 + gl;
+        const unsigned pos = __ballot_sync(CPD_FULL, i < nr && qb[i] > 0.0f) & gmask;
+        if (pos) found = c0 + (31 - __clz(pos)) - grp * G;
       }
     }
     const int64_t ik = r0 + found;
-    if (lane == 0) {
-      a.out_idx[(int64_t)a.k * a.J + j] = (int32_t)ik;
-      if (a.first) a.out_idx[(int64_t)a.n * a.J + j] = -1;
-    }
+    if (gl == 0 && live) a.out_idx[(int64_t)a.k * a.J + j] = (int32_t)ik;
     __syncwarp();
-    for (int r = lane; r < Rp; r += 32) {
+    for (int r = gl; r < Rp; r += G) {
       const float hn = (r < R) ? hs[r] * a.U[ik * Rp + r] : 0.0f;
       hs[r] = hn;
-      if (!a.last) a.Hs[j * Rp + r] = hn;
+      if (!a.last && live) a.Hs[j * Rp + r] = hn;
     }
     __syncwarp();
     if (a.last) {
       // G_{>k} of the last factor is G^+: leverage of the drawn KRP row
       float acc = 0.0f;
-      for (int p = lane; p < npairs; p += 32) {
+      for (int p = gl; p < npairs; p += G) {
         const int x = pa[p], y = pb[p];
         acc = fmaf((x == y ? 1.0f : 2.0f) * Gs[x * R + y], hs[x] * hs[y], acc);
       }
-      acc = warp_sum(acc);
-      if (lane == 0) {
+      acc = group_sum<G>(acc);
+      if (gl == 0 && live) {
         const double prob = (double)acc / Z;
         if (a.out_p) a.out_p[j] = prob;
         if (a.out_w) a.out_w[j] = 1.0 / ((double)a.J * prob);
@@ -298,19 +310,21 @@ __global__ void sts_first_kernel(const double* __restrict__ cdf, const double* _
   }
 }
 
+constexpr int STS_G = 16;   // lanes per draw in the walk
+
 size_t sts_smem(int R, int F) {
   const int npairs = R * (R + 1) / 2;
   const int npad = (npairs + 3) & ~3;
   const int Rp = cpd_pad4(R);
-  const int per_warp = npad + Rp + ((F + 3) & ~3);
-  return (size_t)R * R * 4 + 2 * (size_t)npad + (size_t)STS_NW * per_warp * 4;
+  const int per_group = npad + Rp + ((F + 3) & ~3);
+  return (size_t)R * R * 4 + 2 * (size_t)npad + (size_t)STS_NW * (32 / STS_G) * per_group * 4;
 }
 
 template <int RB>
 cpd_status launch_draw(cpd_ctx* h, const StsArgs& a) {
   const size_t shm = sts_smem(h->R, h->F);
-  const int64_t blocks = std::min<int64_t>(cpd_ceil_div(a.J, STS_NW), (int64_t)h->num_sms * 16);
-  sts_draw_kernel<RB><<<(unsigned)blocks, STS_NW * 32, shm, h->stream>>>(a);
+  const int64_t blocks = std::min<int64_t>(cpd_ceil_div(a.J, STS_NW * (32 / STS_G)), (int64_t)h->num_sms * 16);
+  sts_draw_kernel<RB, STS_G><<<(unsigned)blocks, STS_NW * 32, shm, h->stream>>>(a);
   CPD_LAUNCH(h, "sts_draw");
   return CPD_OK;
 }
@@ -339,9 +353,9 @@ cpd_status cpd_sts_alloc(cpd_ctx* h) {
   if ((s = cpd_alloc(h, &h->sts_cdf, (size_t)h->Imax)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_blk, (size_t)cpd_ceil_div(h->Imax, 256))) != CPD_OK) return s;
   const int shm = (int)sts_smem(R, h->F);
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<32, STS_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<64, STS_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<128, STS_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
   const int lshm = h->F * R * 4;
   CPD_CUDA(h, cudaFuncSetAttribute(sts_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lshm));
   return CPD_OK;
