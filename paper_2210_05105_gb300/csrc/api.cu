@@ -47,9 +47,26 @@ __global__ void fill_kernel(double* p, int n, double v) {
 __global__ void bump_kernel(unsigned long long* ctr) { *ctr += 1ull; }
 
 // One mode update of Algorithm 1 (lines 6-8) on the handle's stream.
-cpd_status mode_update(cpd_ctx* h, int n) {
+// Pseudo-inverse of the Hadamard product of Grams for `mode` on the forked
+// side stream of a captured sweep (it depends only on the factor Grams, so it
+// overlaps the draws and the MTTKRP of the main branch).
+cpd_status fork_pinv(cpd_ctx* h, int mode) {
+  CPD_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+  CPD_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+  cudaStream_t main = h->stream;
+  h->stream = h->side_stream;
+  cpd_status s = cpd_hadamard_pinv(h, mode, h->Gn, h->Gnpinv, h->pinv_scratch2);
+  h->stream = main;
+  if (s != CPD_OK) return s;
+  CPD_CUDA(h, cudaEventRecord(h->ev_join, h->side_stream));
+  return CPD_OK;
+}
+
+// One mode update of Algorithm 1 (lines 6-8).  `forked`: G^+ of this mode was
+// enqueued on the side stream and is joined before the solve.
+cpd_status mode_update(cpd_ctx* h, int n, bool forked = false) {
   cpd_status s;
-  if ((s = cpd_hadamard_pinv(h, n, h->Gn, h->Gnpinv)) != CPD_OK) return s;
+  if (!forked && (s = cpd_hadamard_pinv(h, n, h->Gn, h->Gnpinv)) != CPD_OK) return s;
   if (h->opt.method == CPD_EXACT) {
     if ((s = cpd_exact_mttkrp_launch(h, n, h->Y)) != CPD_OK) return s;
   } else {
@@ -58,15 +75,26 @@ cpd_status mode_update(cpd_ctx* h, int n) {
     if ((s = cpd_sampled_mttkrp_launch(h, n, h->samp_idx, h->samp_w, h->samp_p, J, h->Y, nullptr)) != CPD_OK)
       return s;
   }
+  if (forked) CPD_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   if (h->opt.sketched_gram && h->opt.method != CPD_EXACT && (s = cpd_pinv_into(h, h->Gsk, h->Gnpinv)) != CPD_OK)
     return s;
   if ((s = cpd_solve_renorm(h, n, h->Y, nullptr)) != CPD_OK) return s;
+  // the next mode's G^+ needs this mode's new Gram; fork it before the
+  // sampler refresh so that the two overlap
+  if (forked && n + 1 < h->N && (s = fork_pinv(h, n + 1)) != CPD_OK) return s;
   return cpd_refresh_sampler(h, n);
 }
 
+// One ALS round, captured.  For CP-ARLS-LEV and exact ALS the draws do not
+// read G^+, so each mode's pseudo-inverse runs on a forked branch.
 cpd_status one_sweep(cpd_ctx* h) {
+  const bool fork = h->opt.method != CPD_STS_CP && !h->opt.sketched_gram;
+  if (fork) {
+    cpd_status s = fork_pinv(h, 0);
+    if (s != CPD_OK) return s;
+  }
   for (int n = 0; n < h->N; ++n) {
-    cpd_status s = mode_update(h, n);
+    cpd_status s = mode_update(h, n, fork);
     if (s != CPD_OK) return s;
   }
   bump_kernel<<<1, 1, 0, h->stream>>>(h->sweep_ctr);
@@ -121,6 +149,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_alloc(h, &h->Gpart, std::max((size_t)h->gram_blocks * npairs, 2 * (size_t)R * R))) != CPD_OK)
     return s;
   if ((s = cpd_alloc(h, &h->fit_out, 4)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->pinv_scratch2, 2 * (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->colsq, (size_t)h->gram_blocks * R + 8)) != CPD_OK) return s;
   {
     sumsq_kernel<<<h->gram_blocks, 256, 0, st>>>(h->vals, nnz, h->colsq);
@@ -231,9 +260,12 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   h->stream = (cudaStream_t)cuda_stream;
-  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    delete h;
-    g_create_error = "cudaStreamCreateWithFlags failed";
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    g_create_error = "stream or event creation failed";
+    cpd_destroy(h);
     return CPD_ERR_CUDA;
   }
   cpd_status s = create_impl(h, N, dims, nnz, idx, vals, init_factors);
@@ -433,6 +465,9 @@ void cpd_destroy(cpd_handle h) {
   if (h->sweep_graph) cudaGraphDestroy(h->sweep_graph);
   for (void* p : h->allocs) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

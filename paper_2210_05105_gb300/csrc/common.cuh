@@ -42,6 +42,9 @@ struct cpd_ctx {
   cpd_options opt;
   cudaStream_t stream = nullptr;      // caller's stream (NULL: legacy default stream)
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture the sweep graph
+  cudaStream_t side_stream = nullptr; // forked branch of the captured sweep
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double* pinv_scratch2 = nullptr;    // 2 R^2: scratch of the forked pseudo-inverse
   int device = 0, num_sms = 0;
   std::string last_error;
 
@@ -230,7 +233,7 @@ cpd_status cpd_build_layouts(cpd_ctx* h);
 cpd_status cpd_renormalize_inputs(cpd_ctx* h);
 cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G);
 cpd_status cpd_sketch_gram(cpd_ctx* h, int mode, const int32_t* idx, const double* w, int64_t J);
-cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout);
+cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout, double* scratch = nullptr);
 cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P);
 cpd_status cpd_dense_init(cpd_ctx* h);
 cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_sigma);

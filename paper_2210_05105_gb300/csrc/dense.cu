@@ -650,7 +650,7 @@ static cpd_status launch_pinv(cpd_ctx* h, const PinvJobs& jobs, int njobs) {
 }
 
 // G = *_{k != mode} G_k into Gout and its pseudo-inverse into Pout.
-cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout) {
+cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout, double* scratch) {
   PinvJobs jobs;
   memset(&jobs, 0, sizeof(jobs));
   PinvJob& j = jobs.job[0];
@@ -658,7 +658,7 @@ cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout) {
     if (k != mode) j.in[j.nin++] = h->G[k];
   j.out_had = Gout;
   j.out_pinv = Pout;
-  j.scratch = h->Gpart;   // 2 R^2 doubles at the front of the partial buffer
+  j.scratch = scratch ? scratch : h->Gpart;   // 2 R^2 doubles
   return launch_pinv(h, jobs, 1);
 }
 

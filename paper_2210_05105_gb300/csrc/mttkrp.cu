@@ -103,16 +103,24 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
       // the winning lane writes its column's KRP row (16-byte vectors; rows
       // are independent, so the lanes' gathers overlap) ...
       float4* hrow = reinterpret_cast<float4*>(a.H + (int64_t)u * a.Rp);
-      for (int v4 = 0; v4 < a.Rp / 4; ++v4) {
-        float4 x = make_float4(1.f, 1.f, 1.f, 1.f);
+      for (int v0 = 0; v0 < a.Rp / 4; v0 += 8) {       // 8 vectors in flight per factor
+        float4 x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = make_float4(1.f, 1.f, 1.f, 1.f);
 #pragma unroll
         for (int k = 0; k < CPD_MAX_MODES; ++k) {
           if (k < a.N && k != a.n) {
-            const float4 f = reinterpret_cast<const float4*>(a.U[k] + (int64_t)ik[k] * a.Rp)[v4];
-            x.x *= f.x; x.y *= f.y; x.z *= f.z; x.w *= f.w;
+            const float4* f = reinterpret_cast<const float4*>(a.U[k] + (int64_t)ik[k] * a.Rp) + v0;
+            float4 fv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) fv[q] = (v0 + q < a.Rp / 4) ? __ldg(f + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { x[q].x *= fv[q].x; x[q].y *= fv[q].y; x[q].z *= fv[q].z; x[q].w *= fv[q].w; }
           }
         }
-        hrow[v4] = x;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (v0 + q < a.Rp / 4) hrow[v0 + q] = x[q];
       }
       // ... and marks the chunks c whose first position 32 c lies in its range
       const uint32_t c1 = (off + 31) >> 5, c2 = (off + len - 1) >> 5;

@@ -13,7 +13,7 @@
 // after k:
 //   m(v) = h^T (G^v (*) G_{>k}) h = sum_p c_p G^v_p M_p,  M_p = G_{>k,ab} h_a h_b
 // (c_p = 2 off the diagonal); the walk keeps the absolute target
-// t = u m(root) in float64, goes left iff t < m(left) and otherwise subtracts
+// t = u m(root), goes left iff t < m(left) and otherwise subtracts
 // m(left); at the leaf the row masses q_i = (U_k[i] (*) h)^T G_{>k} (U_k[i] (*) h)
 // are scanned (target rescaled by sum q / m(leaf)).  Masses are float32 sums;
 // the decisions therefore equal the float64 oracle's except within a float32
@@ -180,20 +180,22 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
     __syncwarp();
     const double u = cpd_uniform(a.seed, CPD_STREAM_STS, (unsigned long long)jj, (unsigned long long)a.k,
                                  (unsigned long long)a.n, s);
-    double t = u * (double)mass(1);
+    // float32 target: the masses themselves are float32 sums, so a float64
+    // target would not make the decisions more exact (and FP64 is slow here)
+    float t = (float)u * mass(1);
     int64_t v = 1;
     for (int depth = 0; depth < a.D; ++depth) {
       const int64_t left = 2 * v;
       const float mL = mass(left);
       const int64_t rfirst = (((left + 1) << (a.D - depth - 1)) - a.L) * a.F;
-      if (t >= (double)mL && rfirst < a.I) { t -= (double)mL; v = left + 1; }
+      if (t >= mL && rfirst < a.I) { t -= mL; v = left + 1; }
       else v = left;
     }
     const int64_t r0 = (v - a.L) * a.F;
     const int nr = (int)(a.I - r0 < a.F ? a.I - r0 : a.F);
     const float mleaf = mass(v);
     // row masses of the leaf, rows gl, gl + G, ... of the group
-    double qpart = 0.0;
+    float qpart = 0.0f;
     for (int i = gl; i < a.F; i += G) {
       float q = 0.0f;
       if (i < nr) {
@@ -213,21 +215,21 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
         }
         qb[i] = q;
       }
-      qpart += (double)q;
+      qpart += q;
     }
     __syncwarp();
-    const double qs = group_sum<G>(qpart);
-    const double tl = mleaf > 0.0f ? t * (qs / (double)mleaf) : 0.0;
+    const float qs = group_sum<G>(qpart);
+    const float tl = mleaf > 0.0f ? t * (qs / mleaf) : 0.0f;
     int found = -1;
-    double carry = 0.0;
+    float carry = 0.0f;
     const unsigned gmask = (G == 32) ? CPD_FULL : (((1u << G) - 1u) << (grp * G));
     for (int c0 = 0; c0 < a.F; c0 += G) {
       const int i = c0 + gl;
-      const double qd = (i < nr) ? (double)qb[i] : 0.0;
-      double cum = qd;
+      const float qd = (i < nr) ? qb[i] : 0.0f;
+      float cum = qd;
 #pragma unroll
       for (int o = 1; o < G; o <<= 1) {
-        const double y = __shfl_up_sync(CPD_FULL, cum, o, G);
+        const float y = __shfl_up_sync(CPD_FULL, cum, o, G);
         if (gl >= o) cum += y;
       }
       cum += carry;
@@ -235,14 +237,16 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
       if (found < 0 && hit) found = c0 + (__ffs(hit) - 1) - grp * G;
       carry = __shfl_sync(CPD_FULL, cum, G - 1, G);
     }
-    if (found < 0) {              // rounding put the target past the end
-      found = 0;
-      for (int c0 = 0; c0 < a.F; c0 += G) {
-        const int i = c0 + gl;
-        const unsigned pos = __ballot_sync(CPD_FULL, i < nr && qb[i] > 0.0f) & gmask;
-        if (pos) found = c0 + (31 - __clz(pos)) - grp * G;
-      }
+    // If rounding put the target past the end, take the last row of nonzero
+    // mass.  Computed by every lane: `found` differs between the lane groups
+    // of a warp, and warp votes must not sit under group-dependent branches.
+    int fallback = 0;
+    for (int c0 = 0; c0 < a.F; c0 += G) {
+      const int i = c0 + gl;
+      const unsigned pos = __ballot_sync(CPD_FULL, i < nr && qb[i] > 0.0f) & gmask;
+      if (pos) fallback = c0 + (31 - __clz(pos)) - grp * G;
     }
+    if (found < 0) found = fallback;
     const int64_t ik = r0 + found;
     if (gl == 0 && live) a.out_idx[(int64_t)a.k * a.J + j] = (int32_t)ik;
     __syncwarp();
