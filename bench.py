@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--method", default="arls", choices=["arls", "sts", "exact"])
     p.add_argument("--sketched", action="store_true", help="solve with the Gram of the draws (Fig. 2, bottom)")
+    p.add_argument("--fast", action="store_true", help="float32 Grams / leverage scores (precision option 1)")
     p.add_argument("--samples", type=int, default=0, help="override J of the workload")
     p.add_argument("--study-J", default="", help="comma-separated J values: print one line per J (runtime breakdown "
                    "and fit after --steps sweeps), the sample-count study of the paper's Figs. 11-12")
@@ -219,7 +220,7 @@ def study_J(args):
     init = [torch.from_numpy(u).cuda() for u in synth.init_factors(dims, R, w["init_seed"])]
     for J in [int(x) for x in args.study_J.split(",")]:
         h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
-                           sketched_gram=args.sketched)
+                           sketched_gram=args.sketched, fast=args.fast)
         cpd.cpd_als_sweep(h, args.warmup)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -266,7 +267,7 @@ def ours(args, world, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
-                       sketched_gram=args.sketched)
+                       sketched_gram=args.sketched, fast=args.fast)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
 
@@ -362,7 +363,7 @@ def ours(args, world, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = cpd.cpd_create(dims, idx_h, vals_h, init_h, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
-                            sketched_gram=args.sketched)
+                            sketched_gram=args.sketched, fast=args.fast)
         cpd.cpd_als_sweep(h2, args.steps, sync=False)
         f2 = cpd.cpd_fit(h2)
         outs = [cpd.cpd_get_factors(h2, k, out=torch.empty((dims[k], R), dtype=torch.float32).pin_memory())
@@ -390,6 +391,7 @@ def ours(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": args.workload, "dims": list(dims), "nnz": w["nnz"], "zipf_s": w["zipf"],
                            "values": w["values"], "R": R, "J": J, "method": args.method,
+                           "sketched_gram": args.sketched, "precision": "fast" if args.fast else "exact-draws",
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MB write, outside the events)",
                            "create_seconds": create_s},

@@ -76,7 +76,12 @@ typedef struct {
                               1: with the Gram of the sampled rows, sum_j w_j h_j h_j^T,
                               i.e. the normal equations of the downsampled problem
                               (Fig. 2 bottom, G~^+) */
-  int32_t reserved_i32[7];
+  int32_t precision;       /* 0: Grams, leverage scores and G^+ accurate to float64
+                              (the inverse-CDF draws then equal a float64 statement
+                              of Algorithm 3 up to ties); 1: fast: accumulated in
+                              float32 (draws may differ near CDF boundaries; the
+                              fit stays within the method's noise) */
+  int32_t reserved_i32[6];
 } cpd_options;
 
 /* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */

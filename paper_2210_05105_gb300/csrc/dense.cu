@@ -67,7 +67,7 @@ __global__ void sigma_kernel(const double* __restrict__ part, int nblk, int R, d
 template <int MAXP>
 __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
-    const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart) {
+    const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int fast) {
   extern __shared__ float tile[];                      // TR x R float32
   __shared__ float inv[CPD_MAX_RANK];
   __shared__ unsigned char pa[8320], pb[8320];
@@ -114,12 +114,22 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
       int p = t + m * DTHREADS;
       if (p < npairs) {
         const int a = pa[p], b = pb[p];
+        if (fast) {                      // float32 accumulation (precision option 1)
 #pragma unroll 4
-        for (int rr = 0; rr < TR; rr += 4) {
-          df_fma(ah[m][0], al[m][0], tile[rr * R + a], tile[rr * R + b]);
-          df_fma(ah[m][1], al[m][1], tile[(rr + 1) * R + a], tile[(rr + 1) * R + b]);
-          df_fma(ah[m][2], al[m][2], tile[(rr + 2) * R + a], tile[(rr + 2) * R + b]);
-          df_fma(ah[m][3], al[m][3], tile[(rr + 3) * R + a], tile[(rr + 3) * R + b]);
+          for (int rr = 0; rr < TR; rr += 4) {
+            ah[m][0] = fmaf(tile[rr * R + a], tile[rr * R + b], ah[m][0]);
+            ah[m][1] = fmaf(tile[(rr + 1) * R + a], tile[(rr + 1) * R + b], ah[m][1]);
+            ah[m][2] = fmaf(tile[(rr + 2) * R + a], tile[(rr + 2) * R + b], ah[m][2]);
+            ah[m][3] = fmaf(tile[(rr + 3) * R + a], tile[(rr + 3) * R + b], ah[m][3]);
+          }
+        } else {
+#pragma unroll 4
+          for (int rr = 0; rr < TR; rr += 4) {
+            df_fma(ah[m][0], al[m][0], tile[rr * R + a], tile[rr * R + b]);
+            df_fma(ah[m][1], al[m][1], tile[(rr + 1) * R + a], tile[(rr + 1) * R + b]);
+            df_fma(ah[m][2], al[m][2], tile[(rr + 2) * R + a], tile[(rr + 2) * R + b]);
+            df_fma(ah[m][3], al[m][3], tile[(rr + 3) * R + a], tile[(rr + 3) * R + b]);
+          }
         }
       }
     }
@@ -195,7 +205,7 @@ constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / PINV_THREADS;   // entrie
 // ~2^-48 relative.  Returns false (nothing written) when a float32 pivot is
 // below 1e-6 * max diag or the residual max |I - G X| does not fall below
 // 1e-10 within 6 steps; the float64 path then decides.
-__device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
+__device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
   __shared__ float rowk[PINV_FAST_R], colk[PINV_FAST_R];
   __shared__ float red[PINV_THREADS / 32];
   const int t = threadIdx.x;
@@ -236,7 +246,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
   for (int e = t; e < RR; e += PINV_THREADS) { Xh[e] = W[e]; Xl[e] = 0.0f; }
   __syncthreads();
   bool ok = false;
-  for (int it = 0; it < 6 && !ok; ++it) {
+  for (int it = 0; it < max_newton && !ok; ++it) {
     // W = I - G X with G X in df64
     float emax = 0.0f;
     for (int e = t; e < RR; e += PINV_THREADS) {
@@ -286,7 +296,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
       }
     }
     __syncthreads();
-    ok = em < 1e-10f;
+    ok = em < 1e-10f || max_newton == 1;
   }
   if (!ok) return false;
   for (int e = t; e < RR; e += PINV_THREADS) {
@@ -302,7 +312,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm) {
 // Jacobi eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped.
 // One block; each elimination step copies row and column k aside, then every
 // thread updates its entries (two barriers per step, no serial thread).
-__global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R) {
+__global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R, int fast) {
   extern __shared__ double A[];                     // R x R
   __shared__ double red[40];
   __shared__ int sp[64], sq[64];
@@ -311,7 +321,7 @@ __global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R
   const PinvJob& jb = jobs.job[blockIdx.x];
   const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
-  if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A))) return;
+  if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6)) return;
   for (int e = t; e < RR; e += nt) {
     double v = 1.0;
     for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
@@ -601,16 +611,16 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
   // Gram entries per thread: ceil(npairs / 256) rounded up to 1, 3, 9 or 33
   if (npairs <= DTHREADS)
     normalize_gram_kernel<1><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
-                                                                           h->Gpart);
+                                                                           h->Gpart, h->opt.precision);
   else if (npairs <= 3 * DTHREADS)
     normalize_gram_kernel<3><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
-                                                                           h->Gpart);
+                                                                           h->Gpart, h->opt.precision);
   else if (npairs <= 9 * DTHREADS)
     normalize_gram_kernel<9><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
-                                                                           h->Gpart);
+                                                                           h->Gpart, h->opt.precision);
   else
     normalize_gram_kernel<33><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,
-                                                                            h->Gpart);
+                                                                            h->Gpart, h->opt.precision);
   CPD_LAUNCH(h, "normalize_gram");
   gram_reduce_kernel<<<std::max(1, (R * (R + 1) / 2 + 7) / 8), 256, 0, h->stream>>>(h->Gpart, h->gram_blocks, R, G);
   CPD_LAUNCH(h, "gram_reduce");
@@ -644,7 +654,7 @@ static cpd_status launch_pinv(cpd_ctx* h, const PinvJobs& jobs, int njobs) {
   PhaseTimer pt(h, CPD_PHASE_PINV);
   const int R = h->R;
   size_t shm = pinv_smem(R);
-  pinv_kernel<<<njobs, PINV_THREADS, shm, h->stream>>>(jobs, R);
+  pinv_kernel<<<njobs, PINV_THREADS, shm, h->stream>>>(jobs, R, h->opt.precision);
   CPD_LAUNCH(h, "pinv");
   return CPD_OK;
 }

@@ -26,7 +26,7 @@ constexpr int LEV_THREADS = 256;
 // stores free of bank conflicts.)
 __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
                                                           const double* __restrict__ X, double* __restrict__ ell,
-                                                          double* __restrict__ blk) {
+                                                          double* __restrict__ blk, int fast) {
   extern __shared__ float4 lsm4[];
   const int npairs = R * (R + 1) / 2;
   float2* Xs = reinterpret_cast<float2*>(lsm4);                 // npairs (hi, lo), row-major upper triangle
@@ -52,15 +52,22 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
   if (i < I) {
     float lh = 0.0f, ll = 0.0f;
     int p = 0;
-    for (int a = 0; a < R; ++a) {
-      const float ua = us[a * (LEV_THREADS + 1) + t];
-      for (int b = a; b < R; ++b, ++p) {
-        const float ub = us[b * (LEV_THREADS + 1) + t];
-        const float2 x = Xs[p];
-        const float ph = __fmul_rn(ua, ub);
-        const float pl = __fmaf_rn(ua, ub, -ph);
-        df_fma(lh, ll, ph, x.x);
-        ll = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll));
+    if (fast) {                          // float32 (precision option 1)
+      for (int a = 0; a < R; ++a) {
+        const float ua = us[a * (LEV_THREADS + 1) + t];
+        for (int b = a; b < R; ++b, ++p) lh = fmaf(ua * us[b * (LEV_THREADS + 1) + t], Xs[p].x, lh);
+      }
+    } else {
+      for (int a = 0; a < R; ++a) {
+        const float ua = us[a * (LEV_THREADS + 1) + t];
+        for (int b = a; b < R; ++b, ++p) {
+          const float ub = us[b * (LEV_THREADS + 1) + t];
+          const float2 x = Xs[p];
+          const float ph = __fmul_rn(ua, ub);
+          const float pl = __fmaf_rn(ua, ub, -ph);
+          df_fma(lh, ll, ph, x.x);
+          ll = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll));
+        }
       }
     }
     l = df_value(lh, ll);
@@ -169,7 +176,8 @@ size_t lev_smem(int R) {
 cpd_status quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
                         double* cdf) {
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
-  lev_kernel<<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk);
+  lev_kernel<<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                       h->opt.precision);
   CPD_LAUNCH(h, "lev");
   blk_scan_kernel<<<1, 32, 0, h->stream>>>(blk, nb);
   cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(q, I, blk, cdf);

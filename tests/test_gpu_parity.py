@@ -304,3 +304,25 @@ def test_sketched_gram_end_to_end_fit(cpd):
                      sketched=True)
     assert abs(f_gpu - fits[-1]) < 1e-3
     h.close()
+
+
+def test_fast_precision_fit_and_draws(cpd):
+    """options.precision = 1 (float32 Grams, leverage scores, one Newton step
+    for G^+): draws may leave the float64 law's bins only near boundaries
+    (under 1% of the draws here), and the 5-round fit stays within 1e-3 of
+    the oracle's."""
+    dims, R, J = SMALL["dims"], SMALL["R"], SMALL["J"]
+    idx, vals, init = make_case(dims, SMALL["nnz"], R, seed=1001)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=3001,
+                       fast=True)
+    fs = gpu_factors(cpd, h)
+    samplers = [oc.arls_build(U) for U in fs]
+    gi, _ = cpd.cpd_leverage_sample(h, 1, J, 0)
+    oi, _, _ = oc.arls_draw(samplers, 1, J, 3001, 0)
+    assert np.mean(np.any(gi.cpu().numpy() != oi, axis=0)) < 0.01
+    cpd.cpd_als_sweep(h, 5)
+    f_gpu = cpd.cpd_fit(h)
+    _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], "arls", 5, J=J, seed=3001)
+    assert abs(f_gpu - fits[-1]) < 1e-3
+    h.close()
