@@ -250,6 +250,31 @@ cpd_status cpd_sampled_mttkrp_noalloc(int32_t N, const int64_t* dims, int64_t nn
                                       const int32_t* samp_idx, const double* w, int64_t J,
                                       float* Y, int32_t* status_out, void* cuda_stream);
 
+/*
+ * Batched form: one CUDA graph holding one ALS round of each of T handles
+ * (independent tensors, same device), assigned round-robin to `branches`
+ * parallel graph branches so that small and uneven tensors run concurrently.
+ * The handles must not be used on their own while a batch replays them.
+ * Capturing synchronises the handles' streams; cpd_batch_sweep enqueues
+ * n_sweeps replays on cuda_stream.  Destroying the batch leaves the handles.
+ */
+typedef struct cpd_batch_ctx* cpd_batch;
+cpd_status cpd_batch_create(cpd_handle* handles, int32_t T, int32_t branches, void* cuda_stream,
+                            cpd_batch* out);
+cpd_status cpd_batch_sweep(cpd_batch b, int32_t n_sweeps);
+cpd_status cpd_batch_synchronize(cpd_batch b);
+void cpd_batch_destroy(cpd_batch b);
+
+/*
+ * Autotuner: times the candidate launch shapes on the handle's own data and
+ * keeps the fastest -- sampled-MTTKRP blocks per SM in {2, 4, 8, 16} and, for
+ * STS-CP, lanes per draw in the tree walk in {8, 16, 32}.  The model is not
+ * changed.  Drops the handle's captured round (recaptured on the next
+ * cpd_als_sweep); call before building a batch.  out_choices: host int32[2]
+ * {blocks per SM, lanes per draw}, or NULL.  Synchronises.
+ */
+cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices);
+
 /* Wait for the handle's stream and return the first latched device error. */
 cpd_status cpd_synchronize(cpd_handle h);
 

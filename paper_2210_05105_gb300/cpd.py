@@ -20,6 +20,7 @@ STATUS = {0: "CPD_OK", 1: "CPD_ERR_INVALID_ARG", 2: "CPD_ERR_OUT_OF_RANGE_INDEX"
 EXPORTS = ["cpd_default_options", "cpd_create", "cpd_leverage_sample", "cpd_sampled_mttkrp", "cpd_exact_mttkrp",
            "cpd_gram_solve", "cpd_als_sweep", "cpd_fit", "cpd_get_factors", "cpd_set_factors", "cpd_get_sigma",
            "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_sampled_mttkrp_noalloc", "cpd_synchronize",
+           "cpd_batch_create", "cpd_batch_sweep", "cpd_batch_synchronize", "cpd_batch_destroy", "cpd_autotune",
            "cpd_last_error", "cpd_destroy"]
 PHASES = ["pinv", "draw", "probe", "scan", "spmm", "solve", "gram", "sampler", "exact", "clear"]
 
@@ -68,6 +69,11 @@ def lib():
         "cpd_profile_read": ([_P, _P, _P], st),
         "cpd_sweep_kernel_count": ([_P, _P], st),
         "cpd_synchronize": ([_P], st),
+        "cpd_batch_create": ([_P, i32, i32, _P, ctypes.POINTER(_P)], st),
+        "cpd_batch_sweep": ([_P, i32], st),
+        "cpd_batch_synchronize": ([_P], st),
+        "cpd_batch_destroy": ([_P], None),
+        "cpd_autotune": ([_P, _P], st),
         "cpd_last_error": ([_P], ctypes.c_char_p),
         "cpd_destroy": ([_P], None),
     }
@@ -237,6 +243,51 @@ def cpd_sweep_kernel_count(h):
     n = ctypes.c_int64()
     h._check(lib().cpd_sweep_kernel_count(h.raw, ctypes.cast(ctypes.byref(n), _P)))
     return n.value
+
+
+class Batch:
+    """One graph replaying an ALS round of several handles concurrently."""
+
+    def __init__(self, raw, handles):
+        self.raw, self.handles = raw, handles
+
+    def close(self):
+        if self.raw:
+            lib().cpd_batch_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cpd_batch_create(handles, branches=8, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.raw for h in handles])
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_void_p()
+    st = lib().cpd_batch_create(ctypes.cast(arr, _P), len(handles), int(branches),
+                                ctypes.c_void_p(stream.cuda_stream if stream is not None else 0), ctypes.byref(out))
+    if st != 0:
+        raise CpdError(st, "cpd_batch_create")
+    return Batch(out, list(handles))
+
+
+def cpd_batch_sweep(b, n_sweeps=1, sync=True):
+    st = lib().cpd_batch_sweep(b.raw, int(n_sweeps))
+    if st == 0 and sync:
+        st = lib().cpd_batch_synchronize(b.raw)
+    if st != 0:
+        raise CpdError(st, "cpd_batch_sweep")
+
+
+def cpd_autotune(h):
+    """-> (SpMM blocks per SM, STS lanes per draw) chosen for this handle."""
+    out = (ctypes.c_int32 * 2)()
+    h._check(lib().cpd_autotune(h.raw, ctypes.cast(out, _P)))
+    return out[0], out[1]
 
 
 def cpd_synchronize(h):

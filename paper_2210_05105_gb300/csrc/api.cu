@@ -219,6 +219,10 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
 
 }  // namespace
 
+// One captured ALS round of the handle on its current stream (used by the
+// batch graph, which captures several handles on parallel branches).
+cpd_status cpd_one_sweep(cpd_ctx* h) { return one_sweep(h); }
+
 extern "C" {
 
 cpd_status cpd_default_options(cpd_options* opt) {

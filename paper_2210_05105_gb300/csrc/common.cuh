@@ -110,6 +110,10 @@ struct cpd_ctx {
 
   std::vector<void*> allocs;
 
+  // launch shapes chosen by cpd_autotune
+  int tune_spmm_bps = 8;    // SpMM blocks (of 256 threads) per SM
+  int tune_sts_g = 16;      // lanes per draw in the STS walk
+
   // phase timers (cpd_profile)
   bool profiling = false;
   struct Mark { int phase; cudaEvent_t a, b; };
@@ -241,6 +245,7 @@ cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out);
 // sample.cu
 cpd_status cpd_refresh_sampler(cpd_ctx* h, int mode);
 cpd_status cpd_sample_init(cpd_ctx* h);
+bool cpd_sts_group_fits(cpd_ctx* h, int G);
 cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
                             double* cdf);
 cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep,

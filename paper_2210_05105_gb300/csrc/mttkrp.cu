@@ -284,7 +284,7 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
   }
   {
     PhaseTimer pt(h, CPD_PHASE_SPMM);
-    spmm_kernel<<<h->num_sms * 8, 256, 0, st>>>(a, Y, out_nnz_sel);
+    spmm_kernel<<<h->num_sms * h->tune_spmm_bps, 256, 0, st>>>(a, Y, out_nnz_sel);
     CPD_LAUNCH(h, "spmm");
   }
   if (h->opt.sketched_gram) return cpd_sketch_gram(h, mode, idx, w, J);

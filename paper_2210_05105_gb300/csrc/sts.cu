@@ -314,24 +314,52 @@ __global__ void sts_first_kernel(const double* __restrict__ cdf, const double* _
   }
 }
 
-constexpr int STS_G = 16;   // lanes per draw in the walk
-
-size_t sts_smem(int R, int F) {
+// shared memory of the walk with G lanes per draw
+size_t sts_smem(int R, int F, int G) {
   const int npairs = R * (R + 1) / 2;
   const int npad = (npairs + 3) & ~3;
   const int Rp = cpd_pad4(R);
   const int per_group = npad + Rp + ((F + 3) & ~3);
-  return (size_t)R * R * 4 + 2 * (size_t)npad + (size_t)STS_NW * (32 / STS_G) * per_group * 4;
+  return (size_t)R * R * 4 + 2 * (size_t)npad + (size_t)STS_NW * (32 / G) * per_group * 4;
+}
+
+template <int RB, int G>
+cpd_status launch_draw_g(cpd_ctx* h, const StsArgs& a) {
+  const size_t shm = sts_smem(h->R, h->F, G);
+  const int64_t blocks = std::min<int64_t>(cpd_ceil_div(a.J, STS_NW * (32 / G)), (int64_t)h->num_sms * 16);
+  sts_draw_kernel<RB, G><<<(unsigned)blocks, STS_NW * 32, shm, h->stream>>>(a);
+  CPD_LAUNCH(h, "sts_draw");
+  return CPD_OK;
 }
 
 template <int RB>
 cpd_status launch_draw(cpd_ctx* h, const StsArgs& a) {
-  const size_t shm = sts_smem(h->R, h->F);
-  const int64_t blocks = std::min<int64_t>(cpd_ceil_div(a.J, STS_NW * (32 / STS_G)), (int64_t)h->num_sms * 16);
-  sts_draw_kernel<RB, STS_G><<<(unsigned)blocks, STS_NW * 32, shm, h->stream>>>(a);
-  CPD_LAUNCH(h, "sts_draw");
+  if (h->tune_sts_g == 8) return launch_draw_g<RB, 8>(h, a);
+  if (h->tune_sts_g == 32) return launch_draw_g<RB, 32>(h, a);
+  return launch_draw_g<RB, 16>(h, a);
+}
+
+constexpr size_t STS_SMEM_MAX = 227 * 1024;
+
+template <int RB>
+cpd_status set_draw_smem(cpd_ctx* h) {
+  if (sts_smem(h->R, h->F, 8) <= STS_SMEM_MAX)
+    CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<RB, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sts_smem(h->R, h->F, 8)));
+  if (sts_smem(h->R, h->F, 16) <= STS_SMEM_MAX)
+    CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<RB, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sts_smem(h->R, h->F, 16)));
+  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<RB, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sts_smem(h->R, h->F, 32)));
   return CPD_OK;
 }
+
+}  // namespace
+
+// Whether the walk with G lanes per draw fits in shared memory.
+bool cpd_sts_group_fits(cpd_ctx* h, int G) { return sts_smem(h->R, h->F, G) <= STS_SMEM_MAX; }
+
+namespace {
 
 }  // namespace
 
@@ -340,7 +368,8 @@ cpd_status cpd_sts_alloc(cpd_ctx* h) {
   const int npairs = R * (R + 1) / 2;
   if (h->F < 1 || (int64_t)h->F * R > 16384 || h->F > 1024)
     return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP leaf_rows must satisfy 1 <= F and F * R <= 16384");
-  if (sts_smem(R, h->F) > 227 * 1024) return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP tile exceeds shared memory");
+  if (sts_smem(R, h->F, 32) > STS_SMEM_MAX) return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP tile exceeds shared memory");
+  h->tune_sts_g = sts_smem(R, h->F, 16) <= STS_SMEM_MAX ? 16 : 32;
   cpd_status s;
   for (int k = 0; k < h->N; ++k) {
     const int64_t nleaf = cpd_ceil_div(h->dims[k], h->F);
@@ -356,10 +385,9 @@ cpd_status cpd_sts_alloc(cpd_ctx* h) {
   if ((s = cpd_alloc(h, &h->sts_q, (size_t)h->Imax)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_cdf, (size_t)h->Imax)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_blk, (size_t)cpd_ceil_div(h->Imax, 256))) != CPD_OK) return s;
-  const int shm = (int)sts_smem(R, h->F);
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<32, STS_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<64, STS_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<128, STS_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+  if ((s = set_draw_smem<32>(h)) != CPD_OK) return s;
+  if ((s = set_draw_smem<64>(h)) != CPD_OK) return s;
+  if ((s = set_draw_smem<128>(h)) != CPD_OK) return s;
   const int lshm = h->F * R * 4;
   CPD_CUDA(h, cudaFuncSetAttribute(sts_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lshm));
   return CPD_OK;
