@@ -52,7 +52,10 @@ def parse():
     p.add_argument("--samples", type=int, default=0, help="override J of the workload")
     p.add_argument("--study-J", default="", help="comma-separated J values: print one line per J (runtime breakdown "
                    "and fit after --steps sweeps), the sample-count study of the paper's Figs. 11-12")
-    p.add_argument("--workload", default="zipf_1e5cube_50M", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--workload", default="zipf_1e5cube_50M",
+                   choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
+    p.add_argument("--branches", type=int, default=16, help="concurrent branches of the batched graph")
+    p.add_argument("--no-autotune", action="store_true", help="batched workloads: keep the default launch shapes")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
@@ -202,6 +205,46 @@ def algorithmic(phase, w, stats):
     return "hbm", 0
 
 
+def profile_round(cpd, h, w, method, sweep_id):
+    """One ALS round through the step-wise entry points with the phase timers
+    on: -> ({phase: (ms, launches)}, per-mode MTTKRP statistics)."""
+    import torch
+    dims, J = w["dims"], w["J"]
+    N = len(dims)
+    cpd.cpd_profile(h, True)
+    stats = {"nnz_sel": 0, "J_u": 0, "rows": 0, "I_mean": sum(dims) / N}
+    per_mode = []
+    for n in range(N):
+        if method == "exact":
+            Y = cpd.cpd_exact_mttkrp(h, n)
+            cpd.cpd_gram_solve(h, n, Y)
+            per_mode.append(cpd.cpd_profile_read(h))
+            continue
+        gi, gp = cpd.cpd_leverage_sample(h, n, J, sweep_id)
+        wts = 1.0 / (J * gp)
+        Y, nsel = cpd.cpd_sampled_mttkrp(h, n, gi, wts)
+        cpd.cpd_gram_solve(h, n, Y)
+        per_mode.append(cpd.cpd_profile_read(h))
+        keys = torch.zeros(J, dtype=torch.int64, device="cuda")
+        mult = 1
+        for k in range(N):
+            if k != n:
+                keys += gi[k].long() * mult
+                mult *= dims[k]
+        stats["nnz_sel"] += nsel
+        stats["J_u"] += int(torch.unique(keys).numel())
+        stats["rows"] += int((Y != 0).any(dim=1).sum())
+    cpd.cpd_profile(h, False)
+    phases = {}
+    for ph in per_mode:
+        for k, (ms, n_) in ph.items():
+            a, b = phases.get(k, (0.0, 0))
+            phases[k] = (a + ms, b + n_)
+    for k in ("nnz_sel", "J_u", "rows"):
+        stats[k] = stats[k] / N          # per mode update
+    return phases, stats
+
+
 def workload(args):
     w = dict(synth.WORKLOADS[args.workload])
     if args.samples:
@@ -296,46 +339,7 @@ def ours(args, world, rank, local):
     fit = cpd.cpd_fit(h)
 
     # per-phase breakdown of one round, step-wise entry points (same kernels)
-    sweep_id = args.warmup + args.steps
-    cpd.cpd_profile(h, True)
-    stats = {"nnz_sel": 0, "J_u": 0, "rows": 0, "I_mean": sum(dims) / N}
-    spmm_ms_list = []
-    for n in range(N):
-        if args.method == "exact":
-            Y = cpd.cpd_exact_mttkrp(h, n)
-            cpd.cpd_gram_solve(h, n, Y)
-            stats.setdefault("phases", []).append(cpd.cpd_profile_read(h))
-            continue
-        gi, gp = cpd.cpd_leverage_sample(h, n, J, sweep_id)
-        wts = 1.0 / (J * gp)
-        before = cpd.cpd_profile_read(h)
-        Y, nsel = cpd.cpd_sampled_mttkrp(h, n, gi, wts)
-        ph = cpd.cpd_profile_read(h)
-        spmm_ms_list.append(ph["spmm"][0])
-        for k, v in before.items():
-            ph[k] = (ph[k][0] + v[0], ph[k][1] + v[1])
-        cpd.cpd_gram_solve(h, n, Y)
-        ph2 = cpd.cpd_profile_read(h)
-        for k in ph:
-            ph[k] = (ph[k][0] + ph2[k][0], ph[k][1] + ph2[k][1])
-        stats.setdefault("phases", []).append(ph)
-        keys = torch.zeros(J, dtype=torch.int64, device="cuda")
-        mult = 1
-        for k in range(N):
-            if k != n:
-                keys += gi[k].long() * mult
-                mult *= dims[k]
-        stats["nnz_sel"] += nsel
-        stats["J_u"] += int(torch.unique(keys).numel())
-        stats["rows"] += int((Y != 0).any(dim=1).sum())
-    cpd.cpd_profile(h, False)
-    phases = {}
-    for ph in stats["phases"]:
-        for k, (ms, n_) in ph.items():
-            a, b = phases.get(k, (0.0, 0))
-            phases[k] = (a + ms, b + n_)
-    for k in ("nnz_sel", "J_u", "rows"):
-        stats[k] = stats[k] / N          # per mode update
+    phases, stats = profile_round(cpd, h, w, args.method, args.warmup + args.steps)
     dominant = max((k for k in phases if phases[k][1] > 0), key=lambda k: phases[k][0])
     hbm_peak, peak_kind = peaks()
 
@@ -406,6 +410,169 @@ def ours(args, world, rank, local):
         tdist.destroy_process_group()
 
 
+def batch_bench(args, world, rank, local):
+    """Many uneven tensors: one graph replays an ALS round of all of them on
+    concurrent branches.  value = tensor sweeps per second (T per step); the
+    same handles swept one graph after another give sequential_value."""
+    import torch
+    from paper_2210_05105_gb300 import cpd
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    specs = synth.batch_specs(**synth.BATCH_WORKLOADS[args.workload])
+    T = len(specs)
+    handles, inputs = [], []
+    t0 = time.perf_counter()
+    for s in specs:
+        idx, vals = synth.make_tensor_torch(s["dims"], s["nnz"], s["data_seed"], s["zipf"], s["values"], device="cuda")
+        init = [torch.from_numpy(u).cuda() for u in synth.init_factors(s["dims"], s["R"], s["init_seed"])]
+        inputs.append((idx, vals, init))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for s, (idx, vals, init) in zip(specs, inputs):
+        handles.append(cpd.cpd_create(s["dims"], idx, vals, init, method=args.method, rank=s["R"], samples=s["J"],
+                                      seed=s["sample_seed"], fast=args.fast))
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    choices = [cpd.cpd_autotune(h) for h in handles] if not args.no_autotune else None
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed(step_fn):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for _ in range(args.warmup):
+            step_fn()
+        barrier(world)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            step_fn()
+            stops[i].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [a.elapsed_time(b) for a, b in zip(starts, stops)]
+
+    def seq_step():
+        for h in handles:
+            cpd.cpd_als_sweep(h, 1, sync=False)
+
+    seq_ms = timed(seq_step)
+    b = cpd.cpd_batch_create(handles, branches=args.branches)
+    clk = Clocks(local)
+    clk.start()
+    torch.cuda.nvtx.range_push("timed")
+    bat_ms = timed(lambda: cpd.cpd_batch_sweep(b, 1, sync=False))
+    torch.cuda.nvtx.range_pop()
+    clocks = clk.stop()
+    value, total_ms = replica_throughput(world, args.steps * T, sum(bat_ms))
+    seq_value, _ = replica_throughput(world, args.steps * T, sum(seq_ms))
+    launches = sum(cpd.cpd_sweep_kernel_count(h) for h in handles)
+    fits = [cpd.cpd_fit(h) for h in handles]
+
+    # SpMM roofline over one step-wise round of every tensor
+    hbm_peak, peak_kind = peaks()
+    spmm_ms = spmm_bytes = 0.0
+    phases = {}
+    for s, h in zip(specs, handles):
+        ph, st = profile_round(cpd, h, s, args.method, 1 << 40)
+        for k, (ms, n_) in ph.items():
+            a_, b_ = phases.get(k, (0.0, 0))
+            phases[k] = (a_ + ms, b_ + n_)
+        if args.method != "exact":
+            spmm_ms += ph["spmm"][0]
+            spmm_bytes += algorithmic("spmm", s, st)[1] * len(s["dims"])
+    ach = spmm_bytes / (spmm_ms / 1e3) / 1e9 if spmm_ms else 0.0
+    roofline = {"phase": "spmm", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind,
+                "note": "algorithmic bytes of all %d tensors' SpMM launches / their summed time" % T}
+
+    e2e = None
+    if not args.no_e2e:
+        host = [(i.cpu().pin_memory(), v.cpu().pin_memory(), [u.cpu().pin_memory() for u in ini])
+                for i, v, ini in inputs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs2 = [cpd.cpd_create(s["dims"], i, v, ini, method=args.method, rank=s["R"], samples=s["J"],
+                              seed=s["sample_seed"], fast=args.fast) for s, (i, v, ini) in zip(specs, host)]
+        if choices is not None:
+            for hh in hs2:
+                cpd.cpd_autotune(hh)
+        b2 = cpd.cpd_batch_create(hs2, branches=args.branches)
+        cpd.cpd_batch_sweep(b2, args.steps, sync=False)
+        f2 = [cpd.cpd_fit(hh) for hh in hs2]
+        outs = [[cpd.cpd_get_factors(hh, k, out=torch.empty((s["dims"][k], s["R"]), dtype=torch.float32).pin_memory())
+                 for k in range(len(s["dims"]))] for s, hh in zip(specs, hs2)]
+        e2e_s = allreduce_max(time.perf_counter() - t0, world)
+        b2.close()
+        for hh in hs2:
+            hh.close()
+        h2d = sum(i.numel() * 4 + v.numel() * 4 + sum(u.numel() * 4 for u in ini) for i, v, ini in host)
+        d2h = sum(o.numel() * 4 for os_ in outs for o in os_) + 8 * T
+        e2e = {"value": world * T * args.steps / e2e_s, "unit": "tensor sweeps/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "job": "%d x cpd_create(host COO) + autotune + batched graph + %d rounds + fits + factors to host"
+               % (T, args.steps), "job_seconds": e2e_s, "fit_mean": float(np.mean(f2))}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = batch_oracle(specs, inputs, args.method, budget_s=12.0)
+    b.close()
+    for h in handles:
+        h.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "tensor sweeps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": args.workload, "tensors": T, "nnz_total": sum(s["nnz"] for s in specs),
+                           "orders": "3 and 4 alternating", "R": "16/32/64", "J": "4096-65536 log-uniform",
+                           "method": args.method, "precision": "fast" if args.fast else "exact-draws",
+                           "branches": args.branches, "autotuned": choices is not None,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed between steps (256 MB write, outside the events)",
+                           "generate_seconds": gen_s, "create_seconds": create_s, "autotune_seconds": tune_s},
+                "sequential_value": seq_value, "batched_over_sequential": value / seq_value,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches * args.steps,
+                "phases_ms_per_round": {k: round(v[0], 4) for k, v in phases.items() if v[1]},
+                "fit_mean": float(np.mean(fits)), "fit_min": float(np.min(fits)),
+                "autotune_choices": {"spmm_blocks_per_sm": sorted(set(c[0] for c in choices)) if choices else None,
+                                     "sts_lanes_per_draw": sorted(set(c[1] for c in choices)) if choices else None},
+                "step_ms_median": statistics.median(bat_ms), "sequential_step_ms_median": statistics.median(seq_ms)}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def batch_oracle(specs, inputs, method, budget_s):
+    """The FP64 oracle on a bounded sample of a batched workload: one ALS
+    round of each tensor, smallest first, until budget_s of oracle time."""
+    order = sorted(range(len(specs)), key=lambda t: specs[t]["nnz"])
+    secs, done, nnz = 0.0, 0, 0
+    for t in order:
+        s = specs[t]
+        if inputs is not None:
+            idx, vals = inputs[t][0].cpu().numpy(), inputs[t][1].cpu().numpy()
+        else:
+            idx, vals = synth.make_tensor(s["dims"], s["nnz"], s["data_seed"], s["zipf"], s["values"])
+        init = synth.init_factors(s["dims"], s["R"], s["init_seed"])
+        res = run_oracle(idx, vals, init, s, method, list(range(len(s["dims"]))))
+        secs += res["seconds"]
+        done += 1
+        nnz += s["nnz"]
+        if secs >= budget_s:
+            break
+    return {"value": done / secs, "unit": "tensor sweeps/s", "cores": 1, "kind": "oracle", "seconds": secs,
+            "sample": "one ALS round of the %d smallest of the %d tensors (%d nonzeros), FP64 numpy, 1 thread"
+                      % (done, len(specs), nnz)}
+
+
 def reference(args, world, rank, local):
     """FP64 oracle on the host cores, each step one mode update."""
     if rank != 0:
@@ -437,16 +604,37 @@ def reference(args, world, rank, local):
     print(json.dumps(line))
 
 
+def batch_reference(args, world, rank, local):
+    """Reference arm of a batched workload: the FP64 oracle, each step one ALS
+    round of a bounded sample of the tensors (smallest first)."""
+    if rank != 0:
+        return
+    specs = synth.batch_specs(**synth.BATCH_WORKLOADS[args.workload])
+    for _ in range(args.warmup):
+        batch_oracle(specs, None, args.method, budget_s=2.0)
+    vals = [batch_oracle(specs, None, args.method, budget_s=8.0) for _ in range(args.steps)]
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tensor sweeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "tensors": len(specs), "method": args.method,
+                       "step": "one ALS round of the smallest tensors of the batch, FP64 oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": "tensor sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.cpu_worker:
         cpu_worker(args.cpu_worker)
         return
     world, rank, local = dist()
+    batched = args.workload in synth.BATCH_WORKLOADS
     if args.impl == "reference":
-        reference(args, world, rank, local)
+        (batch_reference if batched else reference)(args, world, rank, local)
     else:
-        ours(args, world, rank, local)
+        (batch_bench if batched else ours)(args, world, rank, local)
 
 
 if __name__ == "__main__":

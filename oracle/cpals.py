@@ -196,10 +196,12 @@ def arls_build(U):
 
 
 def inverse_cdf(cdf, ell, t):
-    """Smallest i with cdf[i] > t; past the end, the last row of nonzero weight."""
+    """Smallest i with cdf[i] > t (Algorithm 3).  Past the end (t rounded up
+    to the total C), the first row whose running sum reaches C, i.e. the last
+    row whose bin has nonzero width.  All weights zero (C = 0): row 0."""
     i = np.searchsorted(cdf, t, side="right")
-    nz = np.nonzero(ell > 0)[0]
-    last = int(nz[-1]) if nz.size else 0
+    C = cdf[-1]
+    last = int(np.searchsorted(cdf, C, side="left")) if C > 0 else 0
     return np.where(i >= cdf.shape[0], last, i).astype(np.int64)
 
 
@@ -224,7 +226,9 @@ def arls_draw(samplers, n, J, seed, sweep, tie_tol=1e-12):
         t = u * s["C"]
         ik = inverse_cdf(s["cdf"], s["ell"], t)
         idx[k] = ik
-        p = p * (s["ell"][ik] / s["C"])
+        # a factor whose scores are all zero has no distribution: its KRP
+        # rows are all zero, the draw keeps row 0 and probability 0
+        p = p * (s["ell"][ik] / s["C"] if s["C"] > 0 else 0.0)
         hi = s["cdf"][ik]
         lo = np.where(ik > 0, s["cdf"][np.maximum(ik - 1, 0)], 0.0)
         tol = tie_tol * s["C"]
@@ -436,8 +440,12 @@ def sketched_gram(factors, n, samp_idx, w):
 
 
 def sample_weights(p, J):
-    """w_j = 1 / (J p_j): diagonal of S^T S for i.i.d. draws with probability p_j."""
-    return 1.0 / (J * np.asarray(p, dtype=np.float64))
+    """w_j = 1 / (J p_j): diagonal of S^T S for i.i.d. draws with probability
+    p_j.  A draw of probability 0 (or undefined, from an all-zero factor, whose
+    KRP rows are all zero) gets weight 0."""
+    p = np.asarray(p, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(p > 0, 1.0 / (J * np.where(p > 0, p, 1.0)), 0.0)
 
 
 def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None, sketched=False):

@@ -271,7 +271,7 @@ def cpd_batch_create(handles, branches=8, stream=None):
     st = lib().cpd_batch_create(ctypes.cast(arr, _P), len(handles), int(branches),
                                 ctypes.c_void_p(stream.cuda_stream if stream is not None else 0), ctypes.byref(out))
     if st != 0:
-        raise CpdError(st, "cpd_batch_create")
+        raise CpdError(st, lib().cpd_last_error(None).decode())
     return Batch(out, list(handles))
 
 

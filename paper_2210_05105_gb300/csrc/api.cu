@@ -1,6 +1,8 @@
 // C ABI of libcpd (include/cpd.h): handle life cycle, the ALS round of
 // Algorithm 1 captured as a CUDA graph, and the step-wise entry points.
 #include "common.cuh"
+#include <map>
+#include <mutex>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -221,6 +223,21 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
 
 // One captured ALS round of the handle on its current stream (used by the
 // batch graph, which captures several handles on parallel branches).
+// Error text of a failed call that returned no handle (cpd_last_error(NULL)).
+void cpd_note_error(const std::string& msg) { g_create_error = msg; }
+
+cpd_status cpd_smem_attr(cpd_ctx* h, const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[std::make_pair(h->device, func)];
+  const size_t want = std::max<size_t>(bytes, 48 * 1024);     // the default limit
+  if (want <= cur) return CPD_OK;
+  CPD_CUDA(h, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want));
+  cur = want;
+  return CPD_OK;
+}
+
 cpd_status cpd_one_sweep(cpd_ctx* h) { return one_sweep(h); }
 
 extern "C" {

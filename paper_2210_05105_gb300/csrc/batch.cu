@@ -14,6 +14,7 @@
 #include <vector>
 
 cpd_status cpd_one_sweep(cpd_ctx* h);
+void cpd_note_error(const std::string& msg);
 
 struct cpd_batch_ctx {
   std::vector<cpd_ctx*> hs;
@@ -64,11 +65,16 @@ static cpd_status capture_batch(cpd_batch_ctx* b) {
   cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (s != CPD_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
+    if (s == CPD_OK) b->last_error = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
     cudaGetLastError();
     return s != CPD_OK ? s : CPD_ERR_CUDA;
   }
   b->graph = g;
-  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return CPD_ERR_CUDA;
+  const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+  if (ei != cudaSuccess) {
+    b->last_error = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+    return CPD_ERR_CUDA;
+  }
   return CPD_OK;
 }
 
@@ -95,7 +101,11 @@ cpd_status cpd_batch_create(cpd_handle* handles, int32_t T, int32_t branches, vo
   }
   if (!ok) { batch_free(b); return CPD_ERR_CUDA; }
   cpd_status s = capture_batch(b);
-  if (s != CPD_OK) { batch_free(b); return s; }
+  if (s != CPD_OK) {
+    cpd_note_error("cpd_batch_create: " + (b->last_error.empty() ? std::string("graph capture failed") : b->last_error));
+    batch_free(b);
+    return s;
+  }
   *out = b;
   return CPD_OK;
 }

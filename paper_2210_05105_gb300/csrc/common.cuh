@@ -148,6 +148,34 @@ template <typename T> cpd_status cpd_alloc(cpd_ctx* h, T** p, size_t count) {
 }
 
 // ---- device helpers ------------------------------------------------------
+// Weight of a draw, w = 1 / (J p) (the diagonal of S^T S); a draw of
+// probability 0 (a factor whose scores are all zero, so every KRP row is
+// zero) gets weight 0 instead of an infinity.
+__device__ __forceinline__ double cpd_weight(int64_t J, double p) { return p > 0.0 ? 1.0 / ((double)J * p) : 0.0; }
+
+// Inverse CDF over non-negative running sums cdf[0..I): the smallest i with
+// cdf[i] > t.  Non-negative doubles order as their bit patterns, so the
+// search compares integers (no FP64 pipe).  If t >= the total C (u C rounded
+// up to C), the first row whose running sum reaches C: the last row with a
+// bin of nonzero width.  Requires C = cdf[I - 1] > 0 and finite.
+__device__ __forceinline__ int64_t cpd_inverse_cdf(const double* __restrict__ cdf, int64_t I, double t) {
+  const long long* cb = reinterpret_cast<const long long*>(cdf);
+  const long long tb = __double_as_longlong(t);
+  int64_t lo = 0, hi = I;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (cb[mid] > tb) hi = mid; else lo = mid + 1;
+  }
+  if (lo < I) return lo;
+  const long long cbits = cb[I - 1];
+  lo = 0; hi = I - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (cb[mid] >= cbits) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ void cpd_set_status(int* status, int code) {
   atomicCAS(status, 0, code);
 }
@@ -236,6 +264,12 @@ cpd_status cpd_build_layouts(cpd_ctx* h);
 // dense.cu
 cpd_status cpd_renormalize_inputs(cpd_ctx* h);
 cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G);
+// Raise (never lower) a kernel's dynamic shared-memory limit on the handle's
+// device; the attribute is per function and shared by every handle.
+cpd_status cpd_smem_attr(cpd_ctx* h, const void* func, size_t bytes);
+bool cpd_gram_tc_supported(const cpd_ctx* h);
+cpd_status cpd_gram_tc_launch(cpd_ctx* h, const float* Uin, float* Uout, int64_t I, const double* sigma, int do_scale,
+                              int* nblk);
 cpd_status cpd_sketch_gram(cpd_ctx* h, int mode, const int32_t* idx, const double* w, int64_t J);
 cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout, double* scratch = nullptr);
 cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 namespace {
 
@@ -202,9 +203,12 @@ constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / PINV_THREADS;   // entrie
 // Fast path for R <= 64 on the float32 pipes: Gauss-Jordan in float32 gives
 // X0 ~ G^{-1}; Newton-Schulz steps X <- X + X (I - G X) with G X formed in
 // df64 (G split exactly into float32 hi + lo) and X carried as df64 bring X to
-// ~2^-48 relative.  Returns false (nothing written) when a float32 pivot is
-// below 1e-6 * max diag or the residual max |I - G X| does not fall below
-// 1e-10 within 6 steps; the float64 path then decides.
+// ~2^-48 relative.  A step taken from residual W = I - G X leaves residual
+// W^2 (plus the df64 floor ~ cond(G) 2^-48), so the iteration stops after the
+// step whose incoming max |W| is below 1e-7: X is then within ~1e-14 of G^{-1}
+// (relative), the accuracy class of a float64 factorisation.  Returns false
+// (nothing written) when a float32 pivot is below 1e-6 * max diag or max |W|
+// does not reach 1e-7 within the allowed steps; the float64 path then decides.
 __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
   __shared__ float rowk[PINV_FAST_R], colk[PINV_FAST_R];
   __shared__ float red[PINV_THREADS / 32];
@@ -271,8 +275,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     float em = 0.0f;
     for (int w = 0; w < PINV_THREADS / 32; ++w) em = fmaxf(em, red[w]);
     if (!isfinite(em)) return false;
-    // X <- X + X W (the correction is small: float32 suffices); once the
-    // residual is below 1e-10 this last step leaves X at the df64 noise level
+    // X <- X + X W (the correction is small: float32 suffices)
     float corr[PINV_PER_T];
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
@@ -296,7 +299,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
       }
     }
     __syncthreads();
-    ok = em < 1e-10f || max_newton == 1;
+    ok = em < 1e-7f || max_newton == 1;
   }
   if (!ok) return false;
   for (int e = t; e < RR; e += PINV_THREADS) {
@@ -606,6 +609,14 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
                             double* G) {
   const int R = h->R;
   PhaseTimer pt(h, CPD_PHASE_GRAM);
+  if (cpd_gram_tc_supported(h) && I > 0) {      // tensor cores (fast precision option)
+    int nblk = 0;
+    cpd_status s = cpd_gram_tc_launch(h, Uin, Uout, I, sigma, do_scale, &nblk);
+    if (s != CPD_OK) return s;
+    gram_reduce_kernel<<<std::max(1, (R * (R + 1) / 2 + 7) / 8), 256, 0, h->stream>>>(h->Gpart, nblk, R, G);
+    CPD_LAUNCH(h, "gram_reduce");
+    return CPD_OK;
+  }
   size_t shm = (size_t)TR * R * sizeof(float);
   const int npairs = R * (R + 1) / 2;
   // Gram entries per thread: ceil(npairs / 256) rounded up to 1, 3, 9 or 33
@@ -733,14 +744,15 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
   size_t s1 = (size_t)TR * R * sizeof(float);
   size_t s2 = pinv_smem(R);
   size_t s3 = (size_t)(2 * R * solve_rb(R)) * sizeof(float);
-  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(normalize_gram_kernel<33>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s1, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s2, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
-  CPD_CUDA(h, cudaFuncSetAttribute(solve_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1)));
+  const std::pair<const void*, size_t> attrs[] = {
+      {(const void*)normalize_gram_kernel<1>, s1}, {(const void*)normalize_gram_kernel<3>, s1},
+      {(const void*)normalize_gram_kernel<9>, s1}, {(const void*)normalize_gram_kernel<33>, s1},
+      {(const void*)pinv_kernel, s2},              {(const void*)solve_kernel<16>, s3},
+      {(const void*)solve_kernel<32>, s3},         {(const void*)solve_kernel<64>, s3},
+      {(const void*)solve_kernel<128>, s3}};
+  for (const auto& a : attrs) {
+    const cpd_status st = cpd_smem_attr(h, a.first, a.second);
+    if (st != CPD_OK) return st;
+  }
   return CPD_OK;
 }

@@ -91,10 +91,27 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
         sl = (sl + 1) & a.dmask;
       }
       atomicAdd(&a.dd_w[sl], (float)w[j]);
+      if (won) u = sl;                      // the slot, until the index is known
+    }
+    // One 64-bit atomic per warp reserves the warp's winners' indices and
+    // nonzero ranges at once; lanes place themselves by a prefix sum.
+    const unsigned wm = __ballot_sync(CPD_FULL, won);
+    if (wm) {
+      const uint32_t mylen = won ? len : 0u;
+      uint32_t incl = mylen;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(CPD_FULL, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const uint32_t tot = __shfl_sync(CPD_FULL, incl, 31);
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(ctr, ((unsigned long long)__popc(wm) << 32) | (unsigned long long)tot);
+      base = __shfl_sync(CPD_FULL, base, 0);
       if (won) {
-        const unsigned long long pk = atomicAdd(ctr, (1ull << 32) | (unsigned long long)len);
-        u = (uint32_t)(pk >> 32);
-        off = (uint32_t)(pk & 0xffffffffull);
+        const uint32_t sl = u;
+        u = (uint32_t)(base >> 32) + (uint32_t)__popc(wm & ((1u << lane) - 1u));
+        off = (uint32_t)(base & 0xffffffffull) + incl - mylen;
         if (u < a.uq_cap) { a.uq_slot[u] = sl; a.uq_off[u] = off; }
         else { cpd_set_status(a.status, CPD_ERR_CAPACITY); won = false; }
       }
@@ -169,22 +186,33 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
       scale = a.dd_w[slot] * __uint_as_float(en.y);
     }
     const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
-    // C lanes cover one row of Rp floats with 16-byte vector reductions, so
-    // one warp instruction updates E = 32 / C selected nonzeros at once.
-    for (int j0 = 0; j0 < cnt; j0 += E) {
-      const int jj = j0 + sub;
-      const int src = jj < 32 ? jj : 31;
-      const uint32_t rj = __shfl_sync(CPD_FULL, row, src);
-      const float sj = __shfl_sync(CPD_FULL, scale, src);
-      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
-      if (sub < E && jj < cnt) {
-        for (int qq = q; qq < C; qq += 32) {
-          const float4 hv = reinterpret_cast<const float4*>(a.H + (int64_t)uj * a.Rp)[qq];
-          float* yp = Y + (int64_t)rj * a.Rp + 4 * qq;
-          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj * hv.x), "f"(sj * hv.y),
-                       "f"(sj * hv.z), "f"(sj * hv.w)
-                       : "memory");
-        }
+    // C lanes cover one row of Rp floats (C <= 32 since R <= 128) with
+    // 16-byte vector reductions, so one warp instruction updates E = 32 / C
+    // selected nonzeros at once.  Four such groups are in flight per lane:
+    // their KRP-row loads are issued before any of their reductions.
+    const float4* H4 = reinterpret_cast<const float4*>(a.H);
+    for (int j0 = 0; j0 < cnt; j0 += 4 * E) {
+      float4 hv[4];
+      float sj[4];
+      uint32_t rj[4];
+      bool act[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = j0 + u * E + sub;
+        const int src = jj < 32 ? jj : 31;
+        rj[u] = __shfl_sync(CPD_FULL, row, src);
+        sj[u] = __shfl_sync(CPD_FULL, scale, src);
+        const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
+        act[u] = sub < E && jj < cnt;
+        hv[u] = act[u] ? H4[(int64_t)uj * C + q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!act[u]) continue;
+        float* yp = Y + (int64_t)rj[u] * a.Rp + 4 * q;
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj[u] * hv[u].x),
+                     "f"(sj[u] * hv[u].y), "f"(sj[u] * hv[u].z), "f"(sj[u] * hv[u].w)
+                     : "memory");
       }
     }
   }

@@ -133,7 +133,8 @@ struct DrawArgs {
 };
 
 // Algorithm 3 with one processor: per factor k != n, i_k = smallest i with
-// cdf_k[i] > u * C_k (past the end: last row of nonzero score).
+// cdf_k[i] > u * C_k (past the end: the row where the running sum reaches C_k).
+// A factor with C_k = 0 (all scores zero) draws row 0 with probability 0.
 __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long* __restrict__ d_sweep,
                                  unsigned long long h_sweep, int32_t* __restrict__ out_idx,
                                  double* __restrict__ out_p, double* __restrict__ out_w) {
@@ -145,26 +146,19 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
       const double* cdf = a.cdf[k];
       const int64_t I = a.dims[k];
       const double C = cdf[I - 1];
+      if (!(C > 0.0) || !isfinite(C)) {     // all scores zero: no distribution, weight 0
+        out_idx[(int64_t)k * J + j] = 0;
+        p = 0.0;
+        continue;
+      }
       const double t = cpd_uniform(a.seed, CPD_STREAM_ARLS, (unsigned long long)j, (unsigned long long)k,
                                    (unsigned long long)a.n, s) * C;
-      // first index in [lo, hi) with cdf > t; non-negative doubles order as
-      // their bit patterns, so the search compares integers (no FP64 pipe)
-      const long long tb = __double_as_longlong(t);
-      const long long* cb = reinterpret_cast<const long long*>(cdf);
-      int64_t lo = 0, hi = I;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (cb[mid] > tb) hi = mid; else lo = mid + 1;
-      }
-      if (lo >= I) {
-        lo = I - 1;
-        while (lo > 0 && !(a.ell[k][lo] > 0.0)) --lo;
-      }
+      const int64_t lo = cpd_inverse_cdf(cdf, I, t);
       out_idx[(int64_t)k * J + j] = (int32_t)lo;
       p *= a.ell[k][lo] / C;
     }
     if (out_p) out_p[j] = p;
-    if (out_w) out_w[j] = 1.0 / ((double)J * p);
+    if (out_w) out_w[j] = cpd_weight(J, p);
   }
 }
 
@@ -202,7 +196,7 @@ cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double*
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
 // once, outside any stream capture).
 cpd_status cpd_sample_init(cpd_ctx* h) {
-  CPD_CUDA(h, cudaFuncSetAttribute(lev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem(h->R)));
+  { const cpd_status st_ = cpd_smem_attr(h, (const void*)lev_kernel, lev_smem(h->R)); if (st_ != CPD_OK) return st_; }
   return CPD_OK;
 }
 

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
       if (gl == 0 && live) {
         const double prob = (double)acc / Z;
         if (a.out_p) a.out_p[j] = prob;
-        if (a.out_w) a.out_w[j] = 1.0 / ((double)a.J * prob);
+        if (a.out_w) a.out_w[j] = cpd_weight(a.J, prob);
       }
     }
     __syncwarp();
@@ -287,25 +287,16 @@ __global__ void sts_first_kernel(const double* __restrict__ cdf, const double* _
   const unsigned long long s = d_sweep ? *d_sweep : h_sweep;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
     const double C = cdf[I - 1];
+    const bool degenerate = !(C > 0.0) || !isfinite(C);    // all row masses zero
     const double t = cpd_uniform(seed, CPD_STREAM_STS, (unsigned long long)j, (unsigned long long)k,
                                  (unsigned long long)n, s) * C;
-    const long long tb = __double_as_longlong(t);         // non-negative: bit order = value order
-    const long long* cb = reinterpret_cast<const long long*>(cdf);
-    int64_t lo = 0, hi = I;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (cb[mid] > tb) hi = mid; else lo = mid + 1;
-    }
-    if (lo >= I) {
-      lo = I - 1;
-      while (lo > 0 && !(q[lo] > 0.0)) --lo;
-    }
+    const int64_t lo = degenerate ? 0 : cpd_inverse_cdf(cdf, I, t);
     out_idx[(int64_t)k * J + j] = (int32_t)lo;
     out_idx[(int64_t)n * J + j] = -1;
     if (last) {
-      const double prob = q[lo] / *Zp;
+      const double prob = degenerate ? 0.0 : q[lo] / *Zp;
       if (out_p) out_p[j] = prob;
-      if (out_w) out_w[j] = 1.0 / ((double)J * prob);
+      if (out_w) out_w[j] = cpd_weight(J, prob);
     } else {
       const float4* src = reinterpret_cast<const float4*>(U + lo * Rp);
       float4* dst = reinterpret_cast<float4*>(Hs + j * Rp);
@@ -344,13 +335,10 @@ constexpr size_t STS_SMEM_MAX = 227 * 1024;
 template <int RB>
 cpd_status set_draw_smem(cpd_ctx* h) {
   if (sts_smem(h->R, h->F, 8) <= STS_SMEM_MAX)
-    CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<RB, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sts_smem(h->R, h->F, 8)));
+    { const cpd_status st_ = cpd_smem_attr(h, (const void*)sts_draw_kernel<RB, 8>, sts_smem(h->R, h->F, 8)); if (st_ != CPD_OK) return st_; }
   if (sts_smem(h->R, h->F, 16) <= STS_SMEM_MAX)
-    CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<RB, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sts_smem(h->R, h->F, 16)));
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_draw_kernel<RB, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sts_smem(h->R, h->F, 32)));
+    { const cpd_status st_ = cpd_smem_attr(h, (const void*)sts_draw_kernel<RB, 16>, sts_smem(h->R, h->F, 16)); if (st_ != CPD_OK) return st_; }
+  { const cpd_status st_ = cpd_smem_attr(h, (const void*)sts_draw_kernel<RB, 32>, sts_smem(h->R, h->F, 32)); if (st_ != CPD_OK) return st_; }
   return CPD_OK;
 }
 
@@ -389,7 +377,7 @@ cpd_status cpd_sts_alloc(cpd_ctx* h) {
   if ((s = set_draw_smem<64>(h)) != CPD_OK) return s;
   if ((s = set_draw_smem<128>(h)) != CPD_OK) return s;
   const int lshm = h->F * R * 4;
-  CPD_CUDA(h, cudaFuncSetAttribute(sts_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lshm));
+  { const cpd_status st_ = cpd_smem_attr(h, (const void*)sts_leaf_kernel, (size_t)lshm); if (st_ != CPD_OK) return st_; }
   return CPD_OK;
 }
 

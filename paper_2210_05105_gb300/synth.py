@@ -111,6 +111,39 @@ WORKLOADS = {
 }
 
 
+# Many uneven tensors decomposed together (the batched form): order 3 or 4
+# alternating, nnz and dims log-uniform, R from {16, 32, 64}, J log-uniform.
+BATCH_WORKLOADS = {
+    "batch64_uneven": dict(T=64, nnz=(1e4, 5e6), dims=(1e3, 2e6), zipf=1.1, values="uniform",
+                           ranks=(16, 32, 64), J=(4096, 65536), seed=1004, sweeps=20),
+}
+
+
+def batch_specs(T, nnz, dims, zipf, values, ranks, J, seed, sweeps):
+    """Per-tensor workload dicts of a batched workload.  A 4-mode draw whose
+    dims multiply to 2^63 or more (beyond the 64-bit linear index), or that
+    would be denser than 1/8, is drawn again."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo_n, hi_n = np.log(nnz[0]), np.log(nnz[1])
+    lo_d, hi_d = np.log(dims[0]), np.log(dims[1])
+    out = []
+    for t in range(T):
+        N = 3 if t % 2 == 0 else 4
+        while True:
+            d = tuple(int(round(x)) for x in np.exp(rng.uniform(lo_d, hi_d, size=N)))
+            z = int(round(float(np.exp(rng.uniform(lo_n, hi_n)))))
+            total = 1
+            for x in d:
+                total *= x
+            if total < 2 ** 63 and z * 8 <= total:
+                break
+        R = int(ranks[int(rng.integers(0, len(ranks)))])
+        j = int(round(float(np.exp(rng.uniform(np.log(J[0]), np.log(J[1]))))))
+        out.append(dict(dims=d, nnz=z, zipf=zipf, values=values, R=R, J=j, sweeps=sweeps,
+                        data_seed=seed * 1000 + t, init_seed=seed * 1000 + 500 + t, sample_seed=seed * 1000 + 900 + t))
+    return out
+
+
 def make_tensor_torch(dims, nnz, seed, zipf_s=0.0, values="uniform", device="cuda"):
     """Device-side version of the same recipe for the large workloads (torch
     generator on `device`, seeded): returns (idx (N, nnz) int32, vals (nnz,)

@@ -326,3 +326,50 @@ def test_fast_precision_fit_and_draws(cpd):
     _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], "arls", 5, J=J, seed=3001)
     assert abs(f_gpu - fits[-1]) < 1e-3
     h.close()
+
+
+@pytest.mark.parametrize("R,I", [(8, 130), (32, 1000), (20, 777), (64, 5003), (100, 300)])
+def test_fast_precision_gram_tensor_cores(cpd, R, I):
+    """precision = 1 forms factor Grams on the tensor cores (bfloat16 x 3
+    exact split, float32 accumulation; R > 64 keeps the float32 FMA loop):
+    each G_k equals U_k^T U_k of the stored normalised factor to float32
+    accumulation accuracy, and the columns have unit norm."""
+    dims = (I, 90, 70)
+    idx, vals, init = make_case(dims, 4000, R, seed=300 + R)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=500, seed=5,
+                       fast=True)
+    for k in range(3):
+        U = cpd.cpd_get_factors(h, k).double().cpu().numpy()
+        G = cpd.cpd_get_gram(h, k).cpu().numpy()
+        ref = U.T @ U
+        assert np.abs(np.linalg.norm(U, axis=0) - 1.0).max() < 1e-5
+        assert np.abs(G - ref).max() <= 2e-6 * np.abs(np.diag(ref)).max()
+    h.close()
+
+
+@pytest.mark.parametrize("method", ["arls", "sts"])
+def test_zero_factor_draws_weight_zero(cpd, method):
+    """A factor set to zero has no sampling distribution: draws through it
+    carry probability 0 and weight 0, the downsampled MTTKRP is exactly zero
+    (no NaN), and the draw stays an O(log I) search (large I, large J)."""
+    dims, R, J = (200_000, 300, 250), 8, 65536
+    idx, vals, init = make_case(dims, 20000, R, seed=21)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method=method, rank=R, samples=J, seed=9)
+    cpd.cpd_set_factors(h, 0, torch.zeros((dims[0], R), device="cuda"))
+    for n in (1, 2):
+        gi, gp = cpd.cpd_leverage_sample(h, n, J, 0)
+        p = gp.cpu().numpy()
+        assert not np.any(p > 0)
+        gi = gi.cpu().numpy()
+        for k in range(3):
+            if k != n:
+                assert gi[k].min() >= 0 and gi[k].max() < dims[k]
+        w = torch.zeros(J, dtype=torch.float64, device="cuda")
+        Y, _ = cpd.cpd_sampled_mttkrp(h, n, torch.from_numpy(gi).cuda(), w)
+        assert torch.all(Y == 0)
+    cpd.cpd_als_sweep(h, 1)
+    for k in range(3):
+        assert torch.isfinite(cpd.cpd_get_factors(h, k)).all()
+    h.close()

@@ -179,6 +179,40 @@ def test_inverse_cdf_edges():
     assert list(got) == [1, 1, 3, 3, 3, 3]          # zero-weight rows never drawn
 
 
+def test_inverse_cdf_past_end_is_last_nonzero_width_bin():
+    """t rounded up to the total C: the first row whose running sum reaches C.
+    A positive weight absorbed by rounding (bin of zero width) is never drawn,
+    past the end included; all weights zero gives row 0."""
+    ell = np.array([1.0, 1e-20, 0.0])
+    cdf = np.cumsum(ell)
+    assert cdf[1] == cdf[0] == 1.0
+    assert list(oc.inverse_cdf(cdf, ell, np.array([0.5, 1.0]))) == [0, 0]
+    z = np.zeros(4)
+    assert list(oc.inverse_cdf(z, z, np.array([0.0]))) == [0]
+
+
+def test_zero_factor_draws_weight_zero_and_zero_update():
+    """A factor of zeros (e.g. after a sampled MTTKRP that met no nonzero) has
+    no leverage distribution; every KRP row through it is zero, so the exact
+    MTTKRP is zero and the draws carry probability 0 and weight 0 (no NaN)."""
+    rng = np.random.default_rng(3)
+    dims, R, J = (6, 5, 4), 3, 50
+    fs = [oc.renormalize(rng.standard_normal((d, R))) for d in dims]
+    fs[0] = np.zeros_like(fs[0])
+    samplers = [oc.arls_build(U) for U in fs]
+    assert samplers[0]["C"] == 0.0
+    idx, p, _ = oc.arls_draw(samplers, 1, J, seed=5, sweep=0)
+    assert np.all(idx[0] == 0) and np.all(p == 0.0)
+    w = oc.sample_weights(p, J)
+    assert np.all(w == 0.0)
+    coords = np.array(np.meshgrid(*[np.arange(d) for d in dims], indexing="ij")).reshape(3, -1)
+    vals = rng.random(coords.shape[1])
+    Y = oc.sampled_mttkrp(coords, vals, dims, fs, 1, idx, w)
+    assert np.all(Y == 0.0)
+    assert np.all(oc.exact_mttkrp(coords, vals, dims, fs, 1) == 0.0)
+    assert np.all(oc.sample_weights(np.array([0.25, 0.0, np.nan]), 2) == np.array([2.0, 0.0, 0.0]))
+
+
 def test_arls_draw_law_matches_factor_marginals():
     rng = np.random.default_rng(12)
     dims = (7, 5, 6)
