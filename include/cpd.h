@@ -79,9 +79,14 @@ typedef struct {
   int32_t precision;       /* 0: Grams, leverage scores and G^+ accurate to float64
                               (the inverse-CDF draws then equal a float64 statement
                               of Algorithm 3 up to ties); 1: fast: accumulated in
-                              float32 (draws may differ near CDF boundaries; the
-                              fit stays within the method's noise) */
-  int32_t reserved_i32[6];
+                              float32, Grams on the tensor cores (draws may differ
+                              near CDF boundaries; the fit stays within the
+                              method's noise) */
+  int32_t spmm_blocks_per_sm; /* launch shape of the sampled SpMM: blocks per SM in
+                              {1, 2, 4, 8}, each holding an equal share of the SM's
+                              shared memory for hot-row accumulation; 0 = default
+                              (2); cpd_autotune may change it */
+  int32_t reserved_i32[5];
 } cpd_options;
 
 /* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */

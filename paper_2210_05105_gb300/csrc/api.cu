@@ -143,6 +143,9 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
     CPD_CUDA(h, cudaMemcpyAsync(h->idx, idx, (size_t)N * nnz * sizeof(int32_t), kind, st));
     CPD_CUDA(h, cudaMemcpyAsync(h->vals, vals, (size_t)nnz * sizeof(float), kind, st));
   }
+  if (h->opt.spmm_blocks_per_sm) h->tune_spmm_bps = h->opt.spmm_blocks_per_sm;
+  h->hot_cap = cpd_spmm_hot_slots(h->Rp, 1);
+  if ((s = cpd_spmm_init(h)) != CPD_OK) return s;
   if ((s = cpd_build_layouts(h)) != CPD_OK) return s;
 
   // ||T||^2
@@ -263,6 +266,10 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
   if (opt->method < CPD_ARLS_LEV || opt->method > CPD_EXACT) return CPD_ERR_INVALID_ARG;
   if (!init_factors || (nnz > 0 && (!idx || !vals))) return CPD_ERR_INVALID_ARG;
   if (opt->method != CPD_EXACT && opt->samples < 1) return CPD_ERR_INVALID_ARG;
+  {
+    const int b = opt->spmm_blocks_per_sm;
+    if (b != 0 && b != 1 && b != 2 && b != 4 && b != 8) return CPD_ERR_INVALID_ARG;
+  }
   // product of all dims must stay below 2^64 (keys and full linear indices)
   long double prod = 1.0L;
   for (int k = 0; k < N; ++k) {

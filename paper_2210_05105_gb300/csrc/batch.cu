@@ -168,7 +168,7 @@ cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices) {
   cpd_status st = CPD_OK;
   float best = 1e30f, ms = 0.0f;
   int best_bps = h->tune_spmm_bps;
-  for (int bps : {2, 4, 8, 16}) {
+  for (int bps : {1, 2, 4, 8}) {
     h->tune_spmm_bps = bps;
     for (int rep = 0; rep < 2 && st == CPD_OK; ++rep) st = time_modes(false, &ms);   // second run is timed
     if (st != CPD_OK) break;

@@ -32,7 +32,14 @@ struct ModeLayout {
   unsigned long long mask = 0;
   int64_t n_fibers = 0;
   unsigned long long stride[CPD_MAX_MODES] = {0};  // key strides, 0 for mode n
+  // Rows of mode n holding the most nonzeros ("hot" rows, hottest first);
+  // their entries carry x = CPD_HOT_BIT | slot instead of the row, and the
+  // SpMM accumulates them in shared memory before one flush per block.
+  int32_t* hot_rows = nullptr;
+  int n_hot = 0;
 };
+#define CPD_HOT_BIT 0x80000000u
+constexpr int CPD_HOT_MIN_COUNT = 256;   // a row with fewer nonzeros stays in the global path
 
 // Device status codes are cpd_status values; 0 = fine.
 struct cpd_ctx {
@@ -111,7 +118,8 @@ struct cpd_ctx {
   std::vector<void*> allocs;
 
   // launch shapes chosen by cpd_autotune
-  int tune_spmm_bps = 8;    // SpMM blocks (of 256 threads) per SM
+  int tune_spmm_bps = 2;    // SpMM blocks per SM (1024 threads each up to 2, then 2048 / bps)
+  int hot_cap = 0;          // hot-row slots per mode kept by the layout
   int tune_sts_g = 16;      // lanes per draw in the STS walk
 
   // phase timers (cpd_profile)
@@ -267,6 +275,9 @@ cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G);
 // Raise (never lower) a kernel's dynamic shared-memory limit on the handle's
 // device; the attribute is per function and shared by every handle.
 cpd_status cpd_smem_attr(cpd_ctx* h, const void* func, size_t bytes);
+int cpd_spmm_threads(int bps);
+int cpd_spmm_hot_slots(int Rp, int bps);
+cpd_status cpd_spmm_init(cpd_ctx* h);
 bool cpd_gram_tc_supported(const cpd_ctx* h);
 cpd_status cpd_gram_tc_launch(cpd_ctx* h, const float* Uin, float* Uout, int64_t I, const double* sigma, int do_scale,
                               int* nblk);

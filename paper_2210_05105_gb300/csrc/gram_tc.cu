@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   const uint32_t buf_bytes = (uint32_t)MT * 128u * GT_TK * 2u;
   uint32_t ncols = 32;
   while (ncols < (uint32_t)(MT * COLS)) ncols <<= 1;
-  const bool write_back = Uout != Uin;
+  const bool write_back = Uout != Uin || do_scale;
 
   for (int r = t; r < CPD_MAX_RANK; r += GT_THREADS) {
     const double s = (do_scale && r < R) ? sigma[r] : 0.0;

@@ -72,6 +72,42 @@ __global__ void gather_entries_kernel(const int32_t* __restrict__ idx_n, const f
   }
 }
 
+__global__ void count_rows_kernel(const uint2* __restrict__ ent, int64_t nnz, uint32_t* __restrict__ counts) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&counts[ent[e].x], 1u);
+}
+
+// rows with at least `min_count` nonzeros -> (count, row) pairs, any order
+__global__ void hot_candidates_kernel(const uint32_t* __restrict__ counts, int64_t I, uint32_t min_count,
+                                      unsigned long long* __restrict__ keys, uint32_t* __restrict__ rows,
+                                      uint32_t* __restrict__ ncand) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = counts[i];
+    if (c >= min_count) {
+      const uint32_t at = atomicAdd(ncand, 1u);
+      keys[at] = c;
+      rows[at] = (uint32_t)i;
+    }
+  }
+}
+
+// after an ascending sort of the candidates: slot s = the s-th largest count
+__global__ void hot_assign_kernel(const uint32_t* __restrict__ rows_sorted, uint32_t ncand, int H,
+                                  int32_t* __restrict__ hot_rows, uint32_t* __restrict__ code) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < H; s += gridDim.x * blockDim.x) {
+    const uint32_t r = rows_sorted[ncand - 1 - (uint32_t)s];
+    hot_rows[s] = (int32_t)r;
+    code[r] = CPD_HOT_BIT | (uint32_t)s;
+  }
+}
+
+__global__ void hot_mark_kernel(uint2* __restrict__ ent, int64_t nnz, const uint32_t* __restrict__ code) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = code[ent[e].x];
+    if (c & CPD_HOT_BIT) ent[e].x = c;
+  }
+}
+
 __global__ void fiber_begin_kernel(const uint32_t* __restrict__ flags_in, const uint32_t* __restrict__ fid,
                                    int64_t nnz, uint32_t* __restrict__ fbeg) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,6 +232,33 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
     CPD_CUDA(h, cudaMemsetAsync(L.table, 0xff, cap * sizeof(FiberSlot), st));
     table_insert_kernel<<<grid, thr, 0, st>>>(keys, fbeg, nf, (uint32_t)nnz, L.table, L.mask, h->status);
     CPD_LAUNCH(h, "table_insert");
+
+    // hot rows of mode n: count, keep rows with >= CPD_HOT_MIN_COUNT
+    // nonzeros, sort by count, give the hottest hot_cap of them slots
+    if (h->hot_cap > 0) {
+      const int64_t In = h->dims[n];
+      uint32_t* counts = nullptr;
+      CPD_CUDA(h, cudaMallocAsync((void**)&counts, (size_t)In * 4, st));
+      CPD_CUDA(h, cudaMemsetAsync(counts, 0, (size_t)In * 4, st));
+      CPD_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(uint32_t), st));    // candidate counter
+      count_rows_kernel<<<grid, thr, 0, st>>>(L.ent, nnz, counts);
+      const unsigned rgrid = (unsigned)std::min<int64_t>(cpd_ceil_div(In, thr), (int64_t)h->num_sms * 8);
+      hot_candidates_kernel<<<rgrid, thr, 0, st>>>(counts, In, CPD_HOT_MIN_COUNT, keys, perm, flags);
+      CPD_LAUNCH(h, "hot candidates");
+      uint32_t ncand = 0;
+      CPD_CUDA(h, cudaMemcpyAsync(&ncand, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      CPD_CUDA(h, cudaStreamSynchronize(st));
+      if (ncand > 0) {
+        if ((s = cpd_radix_sort_u64(h, keys, perm, ncand, 32, keys_tmp, perm_tmp)) != CPD_OK) return s;
+        const int H = (int)std::min<int64_t>(ncand, h->hot_cap);
+        if ((s = cpd_alloc(h, &L.hot_rows, (size_t)H)) != CPD_OK) return s;
+        hot_assign_kernel<<<cpd_ceil_div(H, 256), 256, 0, st>>>(perm, ncand, H, L.hot_rows, counts);
+        hot_mark_kernel<<<grid, thr, 0, st>>>(L.ent, nnz, counts);
+        CPD_LAUNCH(h, "hot rows");
+        L.n_hot = H;
+      }
+      CPD_CUDA(h, cudaFreeAsync(counts, st));
+    }
   }
   CPD_CUDA(h, cudaFreeAsync(keys, st));
   CPD_CUDA(h, cudaFreeAsync(keys_tmp, st));

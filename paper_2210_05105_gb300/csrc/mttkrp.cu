@@ -34,6 +34,8 @@ struct MArgs {
   uint32_t* counters;
   int* status;
   uint32_t uq_cap;
+  const int32_t* hot_rows;   // row of each hot slot (entries carry CPD_HOT_BIT | slot)
+  int n_hot;                 // hot slots accumulated in shared memory by this launch
 };
 
 __device__ __forceinline__ bool fiber_lookup(const FiberSlot* __restrict__ table, unsigned long long mask,
@@ -146,7 +148,16 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
   }
 }
 
-__global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
+__global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
+  // hot rows: one float row (stride Rp + 1, so rows start in different banks)
+  // per slot, and a touched flag per slot; flushed to Y once per block
+  extern __shared__ float hot_acc[];
+  const int S = a.Rp + 1;
+  const int Hs = a.n_hot;
+  unsigned int* touched = reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * S);
+  for (int i = threadIdx.x; i < Hs * S; i += blockDim.x) hot_acc[i] = 0.0f;
+  for (int i = threadIdx.x; i < Hs; i += blockDim.x) touched[i] = 0u;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -188,16 +199,16 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
     const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
     // C lanes cover one row of Rp floats (C <= 32 since R <= 128) with
     // 16-byte vector reductions, so one warp instruction updates E = 32 / C
-    // selected nonzeros at once.  Four such groups are in flight per lane:
-    // their KRP-row loads are issued before any of their reductions.
+    // selected nonzeros at once.  Two such groups are in flight per lane:
+    // their KRP-row loads are issued before either of their reductions.
     const float4* H4 = reinterpret_cast<const float4*>(a.H);
-    for (int j0 = 0; j0 < cnt; j0 += 4 * E) {
-      float4 hv[4];
-      float sj[4];
-      uint32_t rj[4];
-      bool act[4];
+    for (int j0 = 0; j0 < cnt; j0 += 2 * E) {
+      float4 hv[2];
+      float sj[2];
+      uint32_t rj[2];
+      bool act[2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 2; ++u) {
         const int jj = j0 + u * E + sub;
         const int src = jj < 32 ? jj : 31;
         rj[u] = __shfl_sync(CPD_FULL, row, src);
@@ -207,14 +218,39 @@ __global__ void __launch_bounds__(256) spmm_kernel(MArgs a, float* __restrict__ 
         hv[u] = act[u] ? H4[(int64_t)uj * C + q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 2; ++u) {
         if (!act[u]) continue;
-        float* yp = Y + (int64_t)rj[u] * a.Rp + 4 * q;
+        uint32_t r = rj[u];
+        if (r & CPD_HOT_BIT) {
+          const uint32_t slot = r & ~CPD_HOT_BIT;
+          if ((int)slot < Hs) {
+            float* acc = hot_acc + (size_t)slot * S + 4 * q;
+            atomicAdd(acc + 0, sj[u] * hv[u].x);
+            atomicAdd(acc + 1, sj[u] * hv[u].y);
+            atomicAdd(acc + 2, sj[u] * hv[u].z);
+            atomicAdd(acc + 3, sj[u] * hv[u].w);
+            touched[slot] = 1u;
+            continue;
+          }
+          r = (uint32_t)a.hot_rows[slot];
+        }
+        float* yp = Y + (int64_t)r * a.Rp + 4 * q;
         asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj[u] * hv[u].x),
                      "f"(sj[u] * hv[u].y), "f"(sj[u] * hv[u].z), "f"(sj[u] * hv[u].w)
                      : "memory");
       }
     }
+  }
+  // flush the block's hot rows that it touched
+  __syncthreads();
+  for (int i = threadIdx.x; i < Hs * C; i += blockDim.x) {
+    const int slot = i / C, qq = i - slot * C;
+    if (!touched[slot]) continue;
+    const float* acc = hot_acc + (size_t)slot * S + 4 * qq;
+    float* yp = Y + (int64_t)a.hot_rows[slot] * a.Rp + 4 * qq;
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[1]), "f"(acc[2]),
+                 "f"(acc[3])
+                 : "memory");
   }
 }
 
@@ -270,6 +306,22 @@ __global__ void sketch_rows_kernel(MArgs a, const int32_t* __restrict__ idx, con
   }
 }
 
+}  // namespace
+
+// SpMM launch shape for `bps` blocks per SM: 1024 threads per block up to two
+// blocks, then 2048 / bps; the shared memory of an SM is split evenly among
+// its blocks and holds as many hot rows (Rp + 1 floats and a flag) as fit.
+int cpd_spmm_threads(int bps) { return bps <= 2 ? 1024 : 2048 / bps; }
+int cpd_spmm_hot_slots(int Rp, int bps) {
+  const size_t budget = (size_t)(220 * 1024) / (size_t)std::max(bps, 1);
+  return (int)(budget / ((size_t)(Rp + 1) * 4 + 4));
+}
+cpd_status cpd_spmm_init(cpd_ctx* h) {
+  return cpd_smem_attr(h, (const void*)spmm_kernel, (size_t)cpd_spmm_hot_slots(h->Rp, 1) * ((size_t)(h->Rp + 1) * 4 + 4));
+}
+
+namespace {
+
 MArgs make_args(cpd_ctx* h, int mode) {
   MArgs a;
   memset(&a, 0, sizeof(a));
@@ -312,7 +364,11 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
   }
   {
     PhaseTimer pt(h, CPD_PHASE_SPMM);
-    spmm_kernel<<<h->num_sms * h->tune_spmm_bps, 256, 0, st>>>(a, Y, out_nnz_sel);
+    const int bps = h->tune_spmm_bps;
+    a.n_hot = std::min(h->mode[mode].n_hot, cpd_spmm_hot_slots(h->Rp, bps));
+    a.hot_rows = h->mode[mode].hot_rows;
+    const size_t shm = (size_t)a.n_hot * ((size_t)(h->Rp + 1) * 4 + 4);
+    spmm_kernel<<<h->num_sms * bps, cpd_spmm_threads(bps), shm, st>>>(a, Y, out_nnz_sel);
     CPD_LAUNCH(h, "spmm");
   }
   if (h->opt.sketched_gram) return cpd_sketch_gram(h, mode, idx, w, J);

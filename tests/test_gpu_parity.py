@@ -91,6 +91,33 @@ def test_sampled_mttkrp_matches_oracle(cpd, mode):
     h.close()
 
 
+@pytest.mark.parametrize("R,bps", [(8, 0), (128, 1), (128, 8)])
+def test_sampled_mttkrp_hot_rows(cpd, R, bps):
+    """Zipf rows with thousands of nonzeros: rows that the layout marks hot
+    are accumulated in shared memory (and, past the slots a launch holds --
+    164 hot rows against 105 slots at R = 128 with 8 blocks per SM -- through
+    the global path); the result equals the oracle's for every mode, before
+    and after the autotuner changes the launch shape."""
+    dims, nnz, J = (3000, 400, 300), 300_000, 4000
+    idx, vals, init = make_case(dims, nnz, R, seed=77, zipf=1.1)
+    assert np.bincount(idx[0]).max() > 2000
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=8,
+                       spmm_blocks_per_sm=bps)
+    fs = gpu_factors(cpd, h)
+    for tuned in (False, True):
+        if tuned:
+            cpd.cpd_autotune(h)
+        for mode in range(3):
+            oi, op = _oracle_samples(fs, mode, J, 13, 0)
+            w = 1.0 / (J * op)
+            Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, torch.from_numpy(oi), torch.from_numpy(w))
+            ref = oc.sampled_mttkrp(idx, vals, dims, fs, mode, oi, w)
+            assert rel_frob(Y.cpu().numpy(), ref) <= 1e-5
+            assert nsel == oc.selected_nnz(idx, dims, mode, oi)
+    h.close()
+
+
 def test_sampled_mttkrp_edge_cases(cpd):
     h, idx, vals, init, cfg = _small(cpd)
     fs = gpu_factors(cpd, h)
