@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--workload", default="zipf_1e5cube_50M",
                    choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
     p.add_argument("--branches", type=int, default=16, help="concurrent branches of the batched graph")
+    p.add_argument("--leaf-rows", type=int, default=0, help="STS-CP rows per tree leaf F (0: F = R)")
+    p.add_argument("--autotune", action="store_true", help="run cpd_autotune on the handle before timing")
     p.add_argument("--no-autotune", action="store_true", help="batched workloads: keep the default launch shapes")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -310,9 +312,10 @@ def ours(args, world, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
-                       sketched_gram=args.sketched, fast=args.fast)
+                       sketched_gram=args.sketched, fast=args.fast, leaf_rows=args.leaf_rows)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
+    tuned = cpd.cpd_autotune(h) if args.autotune else None
 
     cpd.cpd_als_sweep(h, args.warmup)
     stream = torch.cuda.current_stream()
@@ -396,6 +399,7 @@ def ours(args, world, rank, local):
                 "config": {"workload": args.workload, "dims": list(dims), "nnz": w["nnz"], "zipf_s": w["zipf"],
                            "values": w["values"], "R": R, "J": J, "method": args.method,
                            "sketched_gram": args.sketched, "precision": "fast" if args.fast else "exact-draws",
+                           "leaf_rows": args.leaf_rows or R, "autotuned": tuned,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MB write, outside the events)",
                            "create_seconds": create_s},

@@ -271,12 +271,14 @@ cpd_status cpd_batch_synchronize(cpd_batch b);
 void cpd_batch_destroy(cpd_batch b);
 
 /*
- * Autotuner: times the candidate launch shapes on the handle's own data and
- * keeps the fastest -- sampled-MTTKRP blocks per SM in {2, 4, 8, 16} and, for
- * STS-CP, lanes per draw in the tree walk in {8, 16, 32}.  The model is not
- * changed.  Drops the handle's captured round (recaptured on the next
- * cpd_als_sweep); call before building a batch.  out_choices: host int32[2]
- * {blocks per SM, lanes per draw}, or NULL.  Synchronises.
+ * Autotuner: times the candidates on the handle's own data and keeps the
+ * fastest -- sampled-MTTKRP blocks per SM in {1, 2, 4, 8} and, for STS-CP,
+ * the tree's leaf size F in {F, R, R/2, R/4, R/8} (trees of at most 8 GiB;
+ * the trees are rebuilt, the sampling law does not depend on F) and lanes
+ * per draw in the tree walk in {8, 16, 32}.  The model is not changed.
+ * Drops the handle's captured round (recaptured on the next cpd_als_sweep);
+ * call before building a batch.  out_choices: host int32[3] {blocks per SM,
+ * lanes per draw, leaf rows F}, or NULL.  Synchronises.
  */
 cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices);
 

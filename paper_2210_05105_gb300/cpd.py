@@ -286,10 +286,10 @@ def cpd_batch_sweep(b, n_sweeps=1, sync=True):
 
 
 def cpd_autotune(h):
-    """-> (SpMM blocks per SM, STS lanes per draw) chosen for this handle."""
-    out = (ctypes.c_int32 * 2)()
+    """-> (SpMM blocks per SM, STS lanes per draw, STS leaf rows F) chosen for this handle."""
+    out = (ctypes.c_int32 * 3)()
     h._check(lib().cpd_autotune(h.raw, ctypes.cast(out, _P)))
-    return out[0], out[1]
+    return out[0], out[1], out[2]
 
 
 def cpd_synchronize(h):

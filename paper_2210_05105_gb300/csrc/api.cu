@@ -183,6 +183,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_alloc(h, &h->Gn, (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Gsk, (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Gnpinv, (size_t)R * R)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->Gnpinv_split, 2 * (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Y, (size_t)h->Imax * Rp)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->Uwork, (size_t)h->Imax * Rp)) != CPD_OK) return s;
 
@@ -228,6 +229,14 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
 // batch graph, which captures several handles on parallel branches).
 // Error text of a failed call that returned no handle (cpd_last_error(NULL)).
 void cpd_note_error(const std::string& msg) { g_create_error = msg; }
+
+// Free one allocation of the handle before cpd_destroy (implicitly synchronises).
+void cpd_free(cpd_ctx* h, void* p) {
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it == h->allocs.end()) return;
+  h->allocs.erase(it);
+  cudaFree(p);
+}
 
 cpd_status cpd_smem_attr(cpd_ctx* h, const void* func, size_t bytes) {
   static std::mutex mu;

@@ -14,6 +14,7 @@
 #include <vector>
 
 cpd_status cpd_one_sweep(cpd_ctx* h);
+cpd_status cpd_sts_refresh(cpd_ctx* h, int k);
 void cpd_note_error(const std::string& msg);
 
 struct cpd_batch_ctx {
@@ -135,13 +136,14 @@ void cpd_batch_destroy(cpd_batch b) {
 }
 
 // Times the candidates of each tunable on the handle's data and keeps the
-// fastest: SpMM blocks per SM in {2, 4, 8, 16}; for STS-CP, lanes per draw
-// in {8, 16, 32} (those that fit in shared memory).  Draws use sweep counter
+// fastest: SpMM blocks per SM in {1, 2, 4, 8}; for STS-CP, the leaf size F
+// in {F, R, R/2, R/4, R/8} and then lanes per draw in {8, 16, 32} (those
+// that fit in shared memory).  Draws use sweep counter
 // 2^62 + trial so they do not repeat the run's draws; the model is unchanged.
 cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices) {
   if (!h) return CPD_ERR_INVALID_ARG;
   if (h->opt.method == CPD_EXACT) {
-    if (out_choices) { out_choices[0] = h->tune_spmm_bps; out_choices[1] = h->tune_sts_g; }
+    if (out_choices) { out_choices[0] = h->tune_spmm_bps; out_choices[1] = h->tune_sts_g; out_choices[2] = h->F; }
     return CPD_OK;
   }
   const int64_t J = h->opt.samples;
@@ -176,6 +178,40 @@ cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices) {
   }
   h->tune_spmm_bps = best_bps;
   if (st == CPD_OK && h->opt.method == CPD_STS_CP) {
+    // leaf rows F (Sec. 4.1: leaves of F rows): a shallower walk against a
+    // longer leaf scan; each candidate rebuilds the trees (sampler refresh
+    // and draws are timed), trees of at most 8 GiB and F >= R / 8
+    auto time_sts = [&](float* ms) -> cpd_status {
+      CPD_CUDA(h, cudaEventRecord(a, h->stream));
+      for (int n = 0; n < h->N; ++n) {
+        cpd_status s;
+        if ((s = cpd_sts_refresh(h, n)) != CPD_OK) return s;
+        if ((s = cpd_hadamard_pinv(h, n, h->Gn, h->Gnpinv)) != CPD_OK) return s;
+        if ((s = cpd_draw(h, n, J, nullptr, (1ull << 62) + n, h->samp_idx, h->samp_p, h->samp_w)) != CPD_OK) return s;
+      }
+      CPD_CUDA(h, cudaEventRecord(z, h->stream));
+      CPD_CUDA(h, cudaEventSynchronize(z));
+      CPD_CUDA(h, cudaEventElapsedTime(ms, a, z));
+      return CPD_OK;
+    };
+    const int F0 = h->F;
+    int best_f = F0;
+    best = 1e30f;
+    std::vector<int> cands = {F0};
+    for (int d = 1; d <= 8; d *= 2) {
+      const int F = std::max(2, h->R / d);
+      if (std::find(cands.begin(), cands.end(), F) == cands.end()) cands.push_back(F);
+    }
+    for (int F : cands) {
+      if (!cpd_sts_leaf_rows_valid(h, F) || cpd_sts_tree_bytes(h, F) > (size_t(8) << 30)) continue;
+      if (F != h->F && (st = cpd_sts_set_leaf_rows(h, F)) != CPD_OK) break;
+      for (int rep = 0; rep < 2 && st == CPD_OK; ++rep) st = time_sts(&ms);
+      if (st != CPD_OK) break;
+      if (ms < best) { best = ms; best_f = F; }
+    }
+    if (st == CPD_OK && best_f != h->F) st = cpd_sts_set_leaf_rows(h, best_f);
+  }
+  if (st == CPD_OK && h->opt.method == CPD_STS_CP) {
     best = 1e30f;
     int best_g = h->tune_sts_g;
     for (int g : {8, 16, 32}) {
@@ -194,7 +230,7 @@ cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices) {
   // the captured round holds the old launch shapes
   if (h->sweep_exec) { cudaGraphExecDestroy(h->sweep_exec); h->sweep_exec = nullptr; }
   if (h->sweep_graph) { cudaGraphDestroy(h->sweep_graph); h->sweep_graph = nullptr; }
-  if (out_choices) { out_choices[0] = h->tune_spmm_bps; out_choices[1] = h->tune_sts_g; }
+  if (out_choices) { out_choices[0] = h->tune_spmm_bps; out_choices[1] = h->tune_sts_g; out_choices[2] = h->F; }
   return cpd_synchronize(h);
 }
 

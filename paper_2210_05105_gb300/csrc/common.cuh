@@ -87,6 +87,7 @@ struct cpd_ctx {
   double* Gsk = nullptr;       // R x R Gram of the last draws (sketched-Gram solve)
   double* Gn = nullptr;        // R x R Hadamard of Grams for the solved mode
   double* Gnpinv = nullptr;    // R x R its pseudo-inverse
+  float* Gnpinv_split = nullptr; // the same as float32 hi (R x R) then lo (R x R), for the solve
   double* Gpart = nullptr;     // Gram partial sums: gram_blocks x R x R
   int gram_blocks = 0;
   double* colsq = nullptr;     // column sum-of-squares partials: gram_blocks x R
@@ -278,6 +279,10 @@ cpd_status cpd_smem_attr(cpd_ctx* h, const void* func, size_t bytes);
 int cpd_spmm_threads(int bps);
 int cpd_spmm_hot_slots(int Rp, int bps);
 cpd_status cpd_spmm_init(cpd_ctx* h);
+void cpd_free(cpd_ctx* h, void* p);
+size_t cpd_sts_tree_bytes(const cpd_ctx* h, int F);
+bool cpd_sts_leaf_rows_valid(const cpd_ctx* h, int F);
+cpd_status cpd_sts_set_leaf_rows(cpd_ctx* h, int F);
 bool cpd_gram_tc_supported(const cpd_ctx* h);
 cpd_status cpd_gram_tc_launch(cpd_ctx* h, const float* Uin, float* Uout, int64_t I, const double* sigma, int do_scale,
                               int* nblk);

@@ -175,6 +175,7 @@ struct PinvJob {
   int nin;
   double* out_had;                  // may be null
   double* out_pinv;
+  float* out_split;                 // may be null: out_pinv as float32 hi (R x R) then lo (R x R)
   double* scratch;                  // 2 R x R float64 (global)
 };
 struct PinvJobs { PinvJob job[2]; };
@@ -315,13 +316,12 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
 // Jacobi eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped.
 // One block; each elimination step copies row and column k aside, then every
 // thread updates its entries (two barriers per step, no serial thread).
-__global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R, int fast) {
+__device__ __forceinline__ void pinv_body(const PinvJob& jb, int R, int fast) {
   extern __shared__ double A[];                     // R x R
   __shared__ double red[40];
   __shared__ int sp[64], sq[64];
   __shared__ double sc[64], ss[64];
   __shared__ double rowk[CPD_MAX_RANK], colk[CPD_MAX_RANK];
-  const PinvJob& jb = jobs.job[blockIdx.x];
   const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
   if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6)) return;
@@ -443,6 +443,22 @@ __global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R
   }
 }
 
+// Every path of pinv_body leaves the block together, so the float32 split of
+// the result (the solve's operand) can follow one barrier later.
+__global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R, int fast) {
+  const PinvJob& jb = jobs.job[blockIdx.x];
+  pinv_body(jb, R, fast);
+  if (jb.out_split) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const double p = jb.out_pinv[e];
+      const float hi = (float)p;
+      jb.out_split[e] = hi;
+      jb.out_split[R * R + e] = (float)(p - (double)hi);
+    }
+  }
+}
+
 // ---- solve: Uw = Y (P_hi + P_lo), float32 with the float64 G^+ split ----
 // Four threads per row, each owning a quarter of the RB (>= Rp) columns;
 // the row of Y in registers, P_hi / P_lo in shared memory read as 16-byte
@@ -451,7 +467,7 @@ __global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R
 // fixed-order sum per block.
 template <int RB>
 __global__ void __launch_bounds__(DTHREADS) solve_kernel(
-    const float* __restrict__ Y, const double* __restrict__ P, float* __restrict__ Uw, int64_t I, int R,
+    const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R,
     int Rp, double* __restrict__ colpart) {
   constexpr int CPT = RB / 4;          // columns per thread
   extern __shared__ float4 sm4[];
@@ -460,12 +476,10 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
   __shared__ double wsq[DTHREADS / 32][CPD_MAX_RANK];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int q = t & 3, rl = t >> 2;
-  for (int e = t; e < R * RB; e += DTHREADS) {
+  for (int e = t; e < R * RB; e += DTHREADS) {     // G^+ as float32 hi + lo (split by pinv_kernel)
     const int a = e / RB, c = e % RB;
-    const double p = c < R ? P[a * R + c] : 0.0;
-    const float hi = (float)p;
-    Phi[e] = hi;
-    Plo[e] = (float)(p - (double)hi);
+    Phi[e] = c < R ? P2[a * R + c] : 0.0f;
+    Plo[e] = c < R ? P2[R * R + a * R + c] : 0.0f;
   }
   for (int c = lane; c < CPD_MAX_RANK; c += 32) wsq[wid][c] = 0.0;
   __syncthreads();
@@ -679,6 +693,7 @@ cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout, d
     if (k != mode) j.in[j.nin++] = h->G[k];
   j.out_had = Gout;
   j.out_pinv = Pout;
+  j.out_split = Pout == h->Gnpinv ? h->Gnpinv_split : nullptr;
   j.scratch = scratch ? scratch : h->Gpart;   // 2 R^2 doubles
   return launch_pinv(h, jobs, 1);
 }
@@ -689,6 +704,7 @@ cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P) {
   jobs.job[0].in[0] = G;
   jobs.job[0].nin = 1;
   jobs.job[0].out_pinv = P;
+  jobs.job[0].out_split = P == h->Gnpinv ? h->Gnpinv_split : nullptr;
   jobs.job[0].scratch = h->Gpart;
   return launch_pinv(h, jobs, 1);
 }
@@ -702,13 +718,13 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     const int rb = solve_rb(R);
     size_t shm = (size_t)(2 * R * rb) * sizeof(float);
     if (rb == 16)
-      solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+      solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else if (rb == 32)
-      solve_kernel<32><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+      solve_kernel<32><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else if (rb == 64)
-      solve_kernel<64><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+      solve_kernel<64><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else
-      solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv, h->Uwork, I, R, h->Rp, h->colsq);
+      solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     CPD_LAUNCH(h, "solve");
     sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
     CPD_LAUNCH(h, "sigma");

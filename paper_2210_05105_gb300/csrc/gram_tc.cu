@@ -8,7 +8,7 @@
 // S = [hi^T; mid^T; lo^T] (3 Rp rows, K running over the rows of U), the MMA
 // computes D = S S^T and G[a][b] is the sum of the 3 x 3 piece blocks of D.
 //
-// Per CTA (one per SM, persistent over 64-row tiles of U): all threads load a
+// Per CTA (up to four per SM, persistent over 64-row tiles of U): all threads load a
 // tile (scaled by 1 / sigma when renormalising, the scaled values written back
 // as the new factor), split it and store the pieces in the no-swizzle K-major
 // core-matrix layout (8 rows x 16 bytes per core matrix); one thread issues
@@ -22,6 +22,7 @@
 // writes a zero partial.
 #include "common.cuh"
 #include <cuda_bf16.h>
+#include <algorithm>
 
 namespace {
 
@@ -61,7 +62,7 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 1)
+__global__ void __launch_bounds__(GT_THREADS)
     gram_tc_kernel(const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
                    const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart,
                    int* __restrict__ status) {
@@ -256,7 +257,15 @@ cpd_status cpd_gram_tc_launch(cpd_ctx* h, const float* Uin, float* Uout, int64_t
     const cpd_status st = cpd_smem_attr(h, (const void*)gram_tc_kernel, shm);
     if (st != CPD_OK) return st;
   }
-  const int grid = h->num_sms;
+  // several CTAs per SM hide the load latency of the staging; they share the
+  // SM's 512 TMEM columns (a CTA whose allocation does not fit waits for one
+  // that finishes), and there is one partial per CTA (h->Gpart holds
+  // gram_blocks = 4 per SM)
+  const int M3 = 3 * h->Rp, MT = (M3 + 127) / 128, COLS = ((M3 + 15) / 16 * 16 + 31) / 32 * 32;
+  int ncols = 32;
+  while (ncols < MT * COLS) ncols <<= 1;
+  const int per_sm = std::max(1, std::min(4, 512 / ncols));
+  const int grid = std::min(h->num_sms * per_sm, h->gram_blocks);
   gram_tc_kernel<<<grid, GT_THREADS, shm, h->stream>>>(Uin, Uout, I, h->R, h->Rp, sigma, do_scale, h->Gpart, h->status);
   CPD_LAUNCH(h, "gram_tc");
   *nblk = grid;

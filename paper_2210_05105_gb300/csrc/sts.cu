@@ -351,34 +351,70 @@ namespace {
 
 }  // namespace
 
-cpd_status cpd_sts_alloc(cpd_ctx* h) {
+// Bytes of the trees of all factors for leaf size F.
+size_t cpd_sts_tree_bytes(const cpd_ctx* h, int F) {
+  const size_t npairs = (size_t)h->R * (h->R + 1) / 2;
+  size_t total = 0;
+  for (int k = 0; k < h->N; ++k) {
+    const int64_t nleaf = cpd_ceil_div(h->dims[k], F);
+    int64_t L = 1;
+    while (L < nleaf) L <<= 1;
+    total += (size_t)(2 * L) * npairs * sizeof(float);
+  }
+  return total;
+}
+
+bool cpd_sts_leaf_rows_valid(const cpd_ctx* h, int F) {
+  return F >= 1 && F <= 1024 && (int64_t)F * h->R <= 16384 && sts_smem(h->R, F, 32) <= STS_SMEM_MAX;
+}
+
+// (Re)allocate the trees for leaf size h->F (the old ones are freed) and set
+// the launch limits that depend on F.
+static cpd_status sts_trees(cpd_ctx* h) {
   const int R = h->R;
   const int npairs = R * (R + 1) / 2;
-  if (h->F < 1 || (int64_t)h->F * R > 16384 || h->F > 1024)
-    return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP leaf_rows must satisfy 1 <= F and F * R <= 16384");
-  if (sts_smem(R, h->F, 32) > STS_SMEM_MAX) return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP tile exceeds shared memory");
-  h->tune_sts_g = sts_smem(R, h->F, 16) <= STS_SMEM_MAX ? 16 : 32;
+  if (!cpd_sts_leaf_rows_valid(h, h->F))
+    return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP leaf_rows must satisfy 1 <= F <= 1024, F * R <= 16384");
+  if (!cpd_sts_group_fits(h, h->tune_sts_g)) h->tune_sts_g = cpd_sts_group_fits(h, 16) ? 16 : 32;
   cpd_status s;
   for (int k = 0; k < h->N; ++k) {
+    if (h->tree32[k]) { cpd_free(h, h->tree32[k]); h->tree32[k] = nullptr; }
     const int64_t nleaf = cpd_ceil_div(h->dims[k], h->F);
     int64_t L = 1;
     while (L < nleaf) L <<= 1;
     h->L[k] = L;
     if ((s = cpd_alloc(h, &h->tree32[k], (size_t)(2 * L) * npairs)) != CPD_OK) return s;
     CPD_CUDA(h, cudaMemsetAsync(h->tree32[k], 0, (size_t)(2 * L) * npairs * sizeof(float), h->stream));
-    if ((s = cpd_alloc(h, &h->sts_ggt[k], (size_t)R * R)) != CPD_OK) return s;
   }
+  if ((s = set_draw_smem<32>(h)) != CPD_OK) return s;
+  if ((s = set_draw_smem<64>(h)) != CPD_OK) return s;
+  if ((s = set_draw_smem<128>(h)) != CPD_OK) return s;
+  return cpd_smem_attr(h, (const void*)sts_leaf_kernel, (size_t)h->F * R * 4);
+}
+
+cpd_status cpd_sts_alloc(cpd_ctx* h) {
+  const int R = h->R;
+  h->tune_sts_g = 16;
+  cpd_status s;
+  if ((s = sts_trees(h)) != CPD_OK) return s;
+  for (int k = 0; k < h->N; ++k)
+    if ((s = cpd_alloc(h, &h->sts_ggt[k], (size_t)R * R)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_Z, 1)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_h, (size_t)std::max<int64_t>(h->opt.samples, 1) * h->Rp)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_q, (size_t)h->Imax)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_cdf, (size_t)h->Imax)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->sts_blk, (size_t)cpd_ceil_div(h->Imax, 256))) != CPD_OK) return s;
-  if ((s = set_draw_smem<32>(h)) != CPD_OK) return s;
-  if ((s = set_draw_smem<64>(h)) != CPD_OK) return s;
-  if ((s = set_draw_smem<128>(h)) != CPD_OK) return s;
-  const int lshm = h->F * R * 4;
-  { const cpd_status st_ = cpd_smem_attr(h, (const void*)sts_leaf_kernel, (size_t)lshm); if (st_ != CPD_OK) return st_; }
   return CPD_OK;
+}
+
+cpd_status cpd_sts_refresh(cpd_ctx* h, int k);
+
+// New leaf size: trees rebuilt from the current factors.
+cpd_status cpd_sts_set_leaf_rows(cpd_ctx* h, int F) {
+  h->F = F;
+  cpd_status s = sts_trees(h);
+  for (int k = 0; k < h->N && s == CPD_OK; ++k) s = cpd_sts_refresh(h, k);
+  return s;
 }
 
 // Algorithm 4 with one processor: leaf Grams, then the levels upward.

@@ -44,8 +44,9 @@ def test_autotune_picks_valid_shapes_and_keeps_results():
         idx, vals, init = make_case(dims, nnz, R, seed=77)
         h1 = create(cpd, dims, idx, vals, init, m, R, J, seed=9)
         h2 = create(cpd, dims, idx, vals, init, m, R, J, seed=9)
-        bps, g = cpd.cpd_autotune(h1)
+        bps, g, F = cpd.cpd_autotune(h1)
         assert bps in (1, 2, 4, 8) and g in (8, 16, 32)
+        assert F in (R, R // 2, R // 4, R // 8)
         cpd.cpd_als_sweep(h1, 3)
         cpd.cpd_als_sweep(h2, 3)
         assert abs(cpd.cpd_fit(h1) - cpd.cpd_fit(h2)) < 1e-3
