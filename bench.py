@@ -207,6 +207,12 @@ def algorithmic(phase, w, stats):
     return "hbm", 0
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel (`dram__bytes_read.sum + dram__bytes_write.sum`, two timed rounds of
+# the same command line), keyed by (workload, method, phase).
+TRAFFIC_BYTES = {("zipf_1e5cube_50M", "arls", "spmm"): 67.98e6}
+
+
 def profile_round(cpd, h, w, method, sweep_id):
     """One ALS round through the step-wise entry points with the phase timers
     on: -> ({phase: (ms, launches)}, per-mode MTTKRP statistics)."""
@@ -359,6 +365,8 @@ def ours(args, world, rank, local):
                 "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind}
 
     roofline = roof("exact" if args.method == "exact" else "spmm")
+    if not args.fast and not args.sketched:
+        roofline["traffic"] = TRAFFIC_BYTES.get((args.workload, args.method, roofline["phase"]))
     roofline_spmm = roofline
 
     # end-to-end through the C ABI from pinned host buffers

@@ -211,7 +211,7 @@ constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / PINV_THREADS;   // entrie
 // (nothing written) when a float32 pivot is below 1e-6 * max diag or max |W|
 // does not reach 1e-7 within the allowed steps; the float64 path then decides.
 __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
-  __shared__ float rowk[PINV_FAST_R], colk[PINV_FAST_R];
+  __shared__ float rowk[2][PINV_FAST_R], colk[2][PINV_FAST_R];
   __shared__ float red[PINV_THREADS / 32];
   const int t = threadIdx.x;
   const int RR = R * R;
@@ -227,27 +227,47 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     const float hi = (float)v;
     Gh[e] = hi;
     Gl[e] = (float)(v - (double)hi);
-    W[e] = hi;
+  }
+  // Gauss-Jordan on the thread's own entries e = t + m * PINV_THREADS, kept
+  // in registers; the owners of row k and column k publish them to a
+  // double-buffered shared copy, so each step needs one barrier
+  int ei[PINV_PER_T], ej[PINV_PER_T];
+  float w[PINV_PER_T];
+#pragma unroll
+  for (int m = 0; m < PINV_PER_T; ++m) {
+    const int e = t + m * PINV_THREADS;
+    ei[m] = e < RR ? e / R : -1;
+    ej[m] = e < RR ? e - ei[m] * R : -1;
   }
   __syncthreads();
+#pragma unroll
+  for (int m = 0; m < PINV_PER_T; ++m) w[m] = ei[m] >= 0 ? Gh[t + m * PINV_THREADS] : 0.0f;
   float maxd = 0.0f;
   for (int a = 0; a < R; ++a) maxd = fmaxf(maxd, fabsf(Gh[a * R + a]));
   for (int k = 0; k < R; ++k) {
-    if (t < R) { rowk[t] = W[k * R + t]; colk[t] = W[t * R + k]; }
-    __syncthreads();
-    const float piv = rowk[k];
-    if (!(piv > 1e-6f * maxd) || !isfinite(piv)) return false;    // uniform
-    const float inv = 1.0f / piv;
-    for (int e = t; e < RR; e += PINV_THREADS) {
-      const int i = e / R, j = e % R;
-      float v;
-      if (i == k) v = (j == k) ? inv : rowk[j] * inv;
-      else if (j == k) v = -colk[i] * inv;
-      else v = fmaf(-colk[i], rowk[j] * inv, W[e]);
-      W[e] = v;
+    const int b = k & 1;
+#pragma unroll
+    for (int m = 0; m < PINV_PER_T; ++m) {
+      if (ei[m] == k) rowk[b][ej[m]] = w[m];
+      if (ej[m] == k) colk[b][ei[m]] = w[m];
     }
     __syncthreads();
+    const float piv = rowk[b][k];
+    if (!(piv > 1e-6f * maxd) || !isfinite(piv)) return false;    // uniform
+    const float inv = 1.0f / piv;
+#pragma unroll
+    for (int m = 0; m < PINV_PER_T; ++m) {
+      const int i = ei[m], j = ej[m];
+      if (i < 0) continue;
+      if (i == k) w[m] = (j == k) ? inv : rowk[b][j] * inv;
+      else if (j == k) w[m] = -colk[b][i] * inv;
+      else w[m] = fmaf(-colk[b][i], rowk[b][j] * inv, w[m]);
+    }
   }
+#pragma unroll
+  for (int m = 0; m < PINV_PER_T; ++m)
+    if (ei[m] >= 0) W[t + m * PINV_THREADS] = w[m];
+  __syncthreads();
   for (int e = t; e < RR; e += PINV_THREADS) { Xh[e] = W[e]; Xl[e] = 0.0f; }
   __syncthreads();
   bool ok = false;
