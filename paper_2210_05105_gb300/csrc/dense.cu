@@ -199,28 +199,61 @@ __device__ double block_sum_d(double v, double* red) {
 
 constexpr int PINV_FAST_R = 64;
 constexpr int PINV_THREADS = 1024;
-constexpr int PINV_PER_T = PINV_FAST_R * PINV_FAST_R / PINV_THREADS;   // entries per thread
+constexpr int PINV_PER_T = 4;   // entries per thread of the fast path (R * R / 4 threads, at least one warp)
 
-// Fast path for R <= 64 on the float32 pipes: Gauss-Jordan in float32 gives
-// X0 ~ G^{-1}; Newton-Schulz steps X <- X + X (I - G X) with G X formed in
-// df64 (G split exactly into float32 hi + lo) and X carried as df64 bring X to
-// ~2^-48 relative.  A step taken from residual W = I - G X leaves residual
-// W^2 (plus the df64 floor ~ cond(G) 2^-48), so the iteration stops after the
-// step whose incoming max |W| is below 1e-7: X is then within ~1e-14 of G^{-1}
+// Unevaluated float32 pairs (hi, lo) with |lo| <= ulp(hi) / 2 (df64).
+struct dd {
+  float h, l;
+};
+__device__ __forceinline__ dd dd_norm(float h, float l) {     // fast two-sum, |h| >= |l|
+  const float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  return dd_norm(p, e);
+}
+__device__ __forceinline__ dd dd_sub(dd a, dd b) {
+  float s, e;
+  df_two_sum(a.h, -b.h, s, e);
+  return dd_norm(s, __fadd_rn(e, __fsub_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.h, -a.l}; }
+// 1 / a: float32 reciprocal r, then r + r (1 - a r) in df64 (~2^-46 relative)
+__device__ __forceinline__ dd dd_recip(dd a) {
+  const float r = 1.0f / a.h;
+  const dd res = dd_sub(dd{1.0f, 0.0f}, dd_mul(a, dd{r, 0.0f}));
+  const dd c = dd_mul(dd{r, 0.0f}, res);
+  float s, e;
+  df_two_sum(r, c.h, s, e);
+  return dd_norm(s, __fadd_rn(e, c.l));
+}
+
+// Fast path for R <= 64 on the float32 pipes: Gauss-Jordan elimination in
+// df64 (G split exactly into float32 hi + lo; each thread keeps its own
+// entries in registers, the owners of row and column k publish them, one
+// barrier per step) gives X ~ G^{-1} to ~cond(G) 2^-44; Newton-Schulz steps
+// X <- X + X (I - G X) with G X in df64 then bring X to ~2^-48 relative.  A
+// step taken from residual W = I - G X leaves residual W^2 (plus the df64
+// floor ~ cond(G) 2^-48), so the iteration stops after the step whose
+// incoming max |W| is below 1e-7: X is then within ~1e-14 of G^{-1}
 // (relative), the accuracy class of a float64 factorisation.  Returns false
-// (nothing written) when a float32 pivot is below 1e-6 * max diag or max |W|
-// does not reach 1e-7 within the allowed steps; the float64 path then decides.
+// (nothing written) when a pivot is at most 1e-9 * max diag (the same test
+// as the float64 elimination, so the eigen-decomposition decides) or max |W|
+// does not reach 1e-7 within the allowed steps.
 __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
-  __shared__ float rowk[2][PINV_FAST_R], colk[2][PINV_FAST_R];
-  __shared__ float red[PINV_THREADS / 32];
-  const int t = threadIdx.x;
+  __shared__ float2 rowk[2][PINV_FAST_R], colk[2][PINV_FAST_R];
+  __shared__ float red[32];
+  const int t = threadIdx.x, nt = blockDim.x;   // R * R <= PINV_PER_T * nt
   const int RR = R * R;
   float* Gh = sm;
   float* Gl = Gh + RR;
   float* Xh = Gl + RR;
   float* Xl = Xh + RR;
   float* W = Xl + RR;
-  for (int e = t; e < RR; e += PINV_THREADS) {
+  for (int e = t; e < RR; e += nt) {
     double v = 1.0;
     for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
     if (jb.out_had) jb.out_had[e] = v;
@@ -228,53 +261,52 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     Gh[e] = hi;
     Gl[e] = (float)(v - (double)hi);
   }
-  // Gauss-Jordan on the thread's own entries e = t + m * PINV_THREADS, kept
-  // in registers; the owners of row k and column k publish them to a
-  // double-buffered shared copy, so each step needs one barrier
   int ei[PINV_PER_T], ej[PINV_PER_T];
-  float w[PINV_PER_T];
+  dd w[PINV_PER_T];
 #pragma unroll
   for (int m = 0; m < PINV_PER_T; ++m) {
-    const int e = t + m * PINV_THREADS;
+    const int e = t + m * nt;
     ei[m] = e < RR ? e / R : -1;
     ej[m] = e < RR ? e - ei[m] * R : -1;
   }
   __syncthreads();
 #pragma unroll
-  for (int m = 0; m < PINV_PER_T; ++m) w[m] = ei[m] >= 0 ? Gh[t + m * PINV_THREADS] : 0.0f;
+  for (int m = 0; m < PINV_PER_T; ++m) {
+    const int e = t + m * nt;
+    w[m] = ei[m] >= 0 ? dd{Gh[e], Gl[e]} : dd{0.0f, 0.0f};
+  }
   float maxd = 0.0f;
   for (int a = 0; a < R; ++a) maxd = fmaxf(maxd, fabsf(Gh[a * R + a]));
   for (int k = 0; k < R; ++k) {
     const int b = k & 1;
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
-      if (ei[m] == k) rowk[b][ej[m]] = w[m];
-      if (ej[m] == k) colk[b][ei[m]] = w[m];
+      if (ei[m] == k) rowk[b][ej[m]] = make_float2(w[m].h, w[m].l);
+      if (ej[m] == k) colk[b][ei[m]] = make_float2(w[m].h, w[m].l);
     }
     __syncthreads();
-    const float piv = rowk[b][k];
-    if (!(piv > 1e-6f * maxd) || !isfinite(piv)) return false;    // uniform
-    const float inv = 1.0f / piv;
+    const dd piv{rowk[b][k].x, rowk[b][k].y};
+    if (!(piv.h > 1e-9f * maxd) || !isfinite(piv.h)) return false;    // uniform
+    const dd inv = dd_recip(piv);
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
       const int i = ei[m], j = ej[m];
       if (i < 0) continue;
-      if (i == k) w[m] = (j == k) ? inv : rowk[b][j] * inv;
-      else if (j == k) w[m] = -colk[b][i] * inv;
-      else w[m] = fmaf(-colk[b][i], rowk[b][j] * inv, w[m]);
+      const dd rj{rowk[b][j].x, rowk[b][j].y}, ci{colk[b][i].x, colk[b][i].y};
+      if (i == k) w[m] = (j == k) ? inv : dd_mul(rj, inv);
+      else if (j == k) w[m] = dd_neg(dd_mul(ci, inv));
+      else w[m] = dd_sub(w[m], dd_mul(ci, dd_mul(rj, inv)));
     }
   }
 #pragma unroll
   for (int m = 0; m < PINV_PER_T; ++m)
-    if (ei[m] >= 0) W[t + m * PINV_THREADS] = w[m];
-  __syncthreads();
-  for (int e = t; e < RR; e += PINV_THREADS) { Xh[e] = W[e]; Xl[e] = 0.0f; }
+    if (ei[m] >= 0) { Xh[t + m * nt] = w[m].h; Xl[t + m * nt] = w[m].l; }
   __syncthreads();
   bool ok = false;
   for (int it = 0; it < max_newton && !ok; ++it) {
     // W = I - G X with G X in df64
     float emax = 0.0f;
-    for (int e = t; e < RR; e += PINV_THREADS) {
+    for (int e = t; e < RR; e += nt) {
       const int i = e / R, j = e % R;
       float ah = 0.0f, al = 0.0f;
       for (int k = 0; k < R; ++k) {
@@ -294,13 +326,13 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     if ((t & 31) == 0) red[t >> 5] = emax;
     __syncthreads();
     float em = 0.0f;
-    for (int w = 0; w < PINV_THREADS / 32; ++w) em = fmaxf(em, red[w]);
+    for (int q = 0; q < nt / 32; ++q) em = fmaxf(em, red[q]);
     if (!isfinite(em)) return false;
     // X <- X + X W (the correction is small: float32 suffices)
     float corr[PINV_PER_T];
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
-      const int e = t + m * PINV_THREADS;
+      const int e = t + m * nt;
       float c = 0.0f;
       if (e < RR) {
         const int i = e / R, j = e % R;
@@ -311,7 +343,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < PINV_PER_T; ++m) {
-      const int e = t + m * PINV_THREADS;
+      const int e = t + m * nt;
       if (e < RR) {
         float sh, se;
         df_two_sum(Xh[e], corr[m], sh, se);
@@ -323,7 +355,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     ok = em < 1e-7f || max_newton == 1;
   }
   if (!ok) return false;
-  for (int e = t; e < RR; e += PINV_THREADS) {
+  for (int e = t; e < RR; e += nt) {
     const int i = e / R, j = e % R;
     jb.out_pinv[e] = 0.5 * (df_value(Xh[e], Xl[e]) + df_value(Xh[j * R + i], Xl[j * R + i]));
   }
@@ -699,7 +731,10 @@ static cpd_status launch_pinv(cpd_ctx* h, const PinvJobs& jobs, int njobs) {
   PhaseTimer pt(h, CPD_PHASE_PINV);
   const int R = h->R;
   size_t shm = pinv_smem(R);
-  pinv_kernel<<<njobs, PINV_THREADS, shm, h->stream>>>(jobs, R, h->opt.precision);
+  // the fast path's work per entry is fixed, so fewer threads with four
+  // entries each issue fewer redundant per-step instructions
+  const int threads = R <= PINV_FAST_R ? std::max(32, (R * R / PINV_PER_T + 31) / 32 * 32) : PINV_THREADS;
+  pinv_kernel<<<njobs, threads, shm, h->stream>>>(jobs, R, h->opt.precision);
   CPD_LAUNCH(h, "pinv");
   return CPD_OK;
 }

@@ -69,6 +69,21 @@ def coo_coordinates(dims, nnz, seed, zipf_s=0.0):
         drawn = drawn[:, np.sort(first)]
 
 
+def planted_values(idx, dims, seed):
+    """Values of a planted rank-16 CP model (N(0,1) factors, seeded) at the
+    coordinates idx (N, nnz), plus Gaussian noise scaled to 10% of the
+    planted values' norm."""
+    rng = np.random.Generator(np.random.PCG64(seed + 4241))
+    A = [rng.standard_normal((int(I), PLANTED_RANK)) for I in dims]
+    m = np.ones((idx.shape[1], PLANTED_RANK))
+    for k in range(len(dims)):
+        m *= A[k][np.asarray(idx[k], dtype=np.int64)]
+    v = m.sum(axis=1)
+    rms = float(np.sqrt(np.mean(v * v))) if v.size else 0.0
+    v = v + rng.standard_normal(v.shape[0]) * (PLANTED_NOISE * rms)
+    return v.astype(np.float32)
+
+
 def coo_values(nnz, seed, kind="uniform"):
     rng = np.random.Generator(np.random.PCG64(seed + 7919))
     if kind == "uniform":
@@ -93,7 +108,7 @@ def init_factors(dims, R, seed):
 
 def make_tensor(dims, nnz, seed, zipf_s=0.0, values="uniform"):
     idx = coo_coordinates(dims, nnz, seed, zipf_s)
-    vals = coo_values(nnz, seed, values)
+    vals = planted_values(idx, dims, seed) if values == "planted16" else coo_values(nnz, seed, values)
     return idx, vals
 
 
@@ -105,10 +120,22 @@ WORKLOADS = {
     "zipf_1e5cube_5M": dict(dims=(100_000, 100_000, 100_000), nnz=5_000_000, zipf=1.1,
                             values="lognormal", R=32, J=65536, sweeps=20,
                             data_seed=1003, init_seed=2003, sample_seed=3003),
+    "zipf_1e5cube_20M": dict(dims=(100_000, 100_000, 100_000), nnz=20_000_000, zipf=1.1,
+                             values="lognormal", R=32, J=65536, sweeps=20,
+                             data_seed=1006, init_seed=2006, sample_seed=3006),
     "zipf_1e5cube_50M": dict(dims=(100_000, 100_000, 100_000), nnz=50_000_000, zipf=1.1,
                              values="lognormal", R=32, J=65536, sweeps=20,
                              data_seed=1002, init_seed=2002, sample_seed=3002),
+    # 4-mode precision-form workload: values of a planted rank-16 CP model at
+    # the drawn coordinates plus Gaussian noise of 10% of their norm (the
+    # tensor's zeros are real zeros, so it is not a rank-16 tensor)
+    "planted16_4mode_200M": dict(dims=(1_000_000, 500_000, 100_000, 1_000), nnz=200_000_000, zipf=1.2,
+                                 values="planted16", R=64, J=65536, sweeps=20,
+                                 data_seed=1005, init_seed=2005, sample_seed=3005),
 }
+
+PLANTED_RANK = 16
+PLANTED_NOISE = 0.1
 
 
 # Many uneven tensors decomposed together (the batched form): order 3 or 4
@@ -218,6 +245,20 @@ def make_tensor_torch(dims, nnz, seed, zipf_s=0.0, values="uniform", device="cud
         vals = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
     elif values == "lognormal":
         vals = torch.randn(nnz, generator=g, device=device, dtype=torch.float32).exp()
+    elif values == "planted16":
+        g2 = torch.Generator(device=device)
+        g2.manual_seed(int(seed) + 4241)
+        A = [torch.randn(I, PLANTED_RANK, generator=g2, device=device) for I in dims]
+        vals = torch.empty(nnz, dtype=torch.float32, device=device)
+        step = 1 << 22
+        for c0 in range(0, nnz, step):
+            c1 = min(nnz, c0 + step)
+            m = torch.ones(c1 - c0, PLANTED_RANK, device=device)
+            for k in range(N):
+                m *= A[k][idx[k, c0:c1].long()]
+            vals[c0:c1] = m.sum(dim=1)
+        rms = torch.sqrt(torch.mean(vals.double() ** 2)).float()
+        vals += torch.randn(nnz, generator=g2, device=device) * (PLANTED_NOISE * rms)
     elif values == "logpoisson":
         x = torch.poisson(torch.full((nnz,), 3.0, device=device), generator=g)
         bad = x == 0
