@@ -40,6 +40,7 @@ __global__ void sts_leaf_kernel(const float* __restrict__ U, int64_t I, int R, i
                                 int64_t nleaf, float* __restrict__ tree) {
   extern __shared__ float rows[];      // F x R
   const int npairs = R * (R + 1) / 2;
+  const int nstride = (npairs + 3) & ~3;
   for (int64_t l = blockIdx.x; l < nleaf; l += gridDim.x) {
     const int64_t r0 = l * F;
     const int nr = (int)(I - r0 < F ? I - r0 : F);
@@ -49,7 +50,7 @@ __global__ void sts_leaf_kernel(const float* __restrict__ U, int64_t I, int R, i
       rows[e] = i < nr ? U[(r0 + i) * Rp + c] : 0.0f;
     }
     __syncthreads();
-    float* out = tree + (L + l) * npairs;
+    float* out = tree + (L + l) * nstride;
     for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
       int a, b;
       pair_of(p, R, a, b);
@@ -60,13 +61,16 @@ __global__ void sts_leaf_kernel(const float* __restrict__ U, int64_t I, int R, i
   }
 }
 
-// One level of the upward sums: nodes [lo, 2 lo).
-__global__ void sts_up_kernel(float* __restrict__ tree, int64_t lo, int npairs) {
-  const int64_t total = lo * npairs;
+// One level of the upward sums: nodes [lo, 2 lo), nstride floats per node
+// (the packed upper triangle padded to a multiple of 4; the padding is 0).
+__global__ void sts_up_kernel(float* __restrict__ tree, int64_t lo, int nstride) {
+  const int64_t total = lo * nstride / 4;
+  float4* t4 = reinterpret_cast<float4*>(tree);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = lo + e / npairs;
-    const int p = (int)(e % npairs);
-    tree[v * npairs + p] = tree[(2 * v) * npairs + p] + tree[(2 * v + 1) * npairs + p];
+    const int64_t v = lo + e / (nstride / 4);
+    const int64_t q = e % (nstride / 4);
+    const float4 x = t4[(2 * v) * (nstride / 4) + q], y = t4[(2 * v + 1) * (nstride / 4) + q];
+    t4[v * (nstride / 4) + q] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
   }
 }
 
@@ -139,7 +143,9 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
   const int npad = (npairs + 3) & ~3;
   unsigned char* pa = reinterpret_cast<unsigned char*>(Gs + R * R);
   unsigned char* pb = pa + npad;
-  float* wbase = reinterpret_cast<float*>(pb + npad);
+  // per-group scratch from the first 16-byte boundary after the pair tables
+  float* wbase = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sm4) +
+                                          (((size_t)R * R * 4 + 2 * (size_t)npad + 15) & ~(size_t)15));
   const int per_group = npad + Rp + ((a.F + 3) & ~3);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane % G;
@@ -160,11 +166,20 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
   const int64_t warp = (int64_t)blockIdx.x * STS_NW + wid;
   const int64_t nwarps = (int64_t)gridDim.x * STS_NW;
 
+  // m(v) = sum_p G^v_p M_p over the node's padded packed triangle, 16-byte
+  // vectors, two accumulators
+  const float4* M4 = reinterpret_cast<const float4*>(M);
   auto mass = [&](int64_t v) -> float {
-    const float* g = a.tree + v * npairs;
-    float acc = 0.0f;
-    for (int p = gl; p < npairs; p += G) acc = fmaf(g[p], M[p], acc);
-    return group_sum<G>(acc);
+    const float4* g4 = reinterpret_cast<const float4*>(a.tree + v * npad);
+    float acc0 = 0.0f, acc1 = 0.0f;
+    for (int q = gl; q < npad / 4; q += G) {
+      const float4 gv = g4[q], mv = M4[q];
+      acc0 = fmaf(gv.x, mv.x, acc0);
+      acc1 = fmaf(gv.y, mv.y, acc1);
+      acc0 = fmaf(gv.z, mv.z, acc0);
+      acc1 = fmaf(gv.w, mv.w, acc1);
+    }
+    return group_sum<G>(acc0 + acc1);
   };
 
   for (int64_t jb = warp * DPW; jb < a.J; jb += nwarps * DPW) {
@@ -173,9 +188,13 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_draw_kernel(StsArgs a) {
     const int64_t jj = live ? j : a.J - 1;           // dead groups shadow a live draw, write nothing
     for (int r = gl; r < Rp; r += G) hs[r] = a.Hs[jj * Rp + r];
     __syncwarp();
-    for (int p = gl; p < npairs; p += G) {
-      const int x = pa[p], y = pb[p];
-      M[p] = (x == y ? 1.0f : 2.0f) * Gs[x * R + y] * hs[x] * hs[y];
+    for (int p = gl; p < npad; p += G) {
+      if (p < npairs) {
+        const int x = pa[p], y = pb[p];
+        M[p] = (x == y ? 1.0f : 2.0f) * Gs[x * R + y] * hs[x] * hs[y];
+      } else {
+        M[p] = 0.0f;
+      }
     }
     __syncwarp();
     const double u = cpd_uniform(a.seed, CPD_STREAM_STS, (unsigned long long)jj, (unsigned long long)a.k,
@@ -311,7 +330,7 @@ size_t sts_smem(int R, int F, int G) {
   const int npad = (npairs + 3) & ~3;
   const int Rp = cpd_pad4(R);
   const int per_group = npad + Rp + ((F + 3) & ~3);
-  return (size_t)R * R * 4 + 2 * (size_t)npad + (size_t)STS_NW * (32 / G) * per_group * 4;
+  return (((size_t)R * R * 4 + 2 * (size_t)npad + 15) & ~(size_t)15) + (size_t)STS_NW * (32 / G) * per_group * 4;
 }
 
 template <int RB, int G>
@@ -353,7 +372,7 @@ namespace {
 
 // Bytes of the trees of all factors for leaf size F.
 size_t cpd_sts_tree_bytes(const cpd_ctx* h, int F) {
-  const size_t npairs = (size_t)h->R * (h->R + 1) / 2;
+  const size_t npairs = (size_t)(((h->R * (h->R + 1) / 2) + 3) & ~3);   // padded node stride
   size_t total = 0;
   for (int k = 0; k < h->N; ++k) {
     const int64_t nleaf = cpd_ceil_div(h->dims[k], F);
@@ -372,7 +391,7 @@ bool cpd_sts_leaf_rows_valid(const cpd_ctx* h, int F) {
 // the launch limits that depend on F.
 static cpd_status sts_trees(cpd_ctx* h) {
   const int R = h->R;
-  const int npairs = R * (R + 1) / 2;
+  const int npairs = ((R * (R + 1) / 2) + 3) & ~3;   // node stride: packed triangle padded to 4
   if (!cpd_sts_leaf_rows_valid(h, h->F))
     return cpd_fail(h, CPD_ERR_INVALID_ARG, "STS-CP leaf_rows must satisfy 1 <= F <= 1024, F * R <= 16384");
   if (!cpd_sts_group_fits(h, h->tune_sts_g)) h->tune_sts_g = cpd_sts_group_fits(h, 16) ? 16 : 32;
@@ -420,16 +439,16 @@ cpd_status cpd_sts_set_leaf_rows(cpd_ctx* h, int F) {
 // Algorithm 4 with one processor: leaf Grams, then the levels upward.
 cpd_status cpd_sts_refresh(cpd_ctx* h, int k) {
   PhaseTimer pt(h, CPD_PHASE_SAMPLER);
-  const int R = h->R, npairs = R * (R + 1) / 2;
+  const int R = h->R, nstride = ((R * (R + 1) / 2) + 3) & ~3;
   const int64_t I = h->dims[k], L = h->L[k];
   const int64_t nleaf = cpd_ceil_div(I, h->F);
   const int grid = (int)std::min<int64_t>(nleaf, (int64_t)h->num_sms * 8);
   sts_leaf_kernel<<<grid, 256, (size_t)h->F * R * 4, h->stream>>>(h->U[k], I, R, h->Rp, h->F, L, nleaf, h->tree32[k]);
   CPD_LAUNCH(h, "sts_leaf");
   for (int64_t lo = L / 2; lo >= 1; lo /= 2) {
-    const int64_t total = lo * npairs;
+    const int64_t total = lo * nstride / 4;
     const int g = (int)std::min<int64_t>(cpd_ceil_div(total, 256), (int64_t)h->num_sms * 8);
-    sts_up_kernel<<<g, 256, 0, h->stream>>>(h->tree32[k], lo, npairs);
+    sts_up_kernel<<<g, 256, 0, h->stream>>>(h->tree32[k], lo, nstride);
     CPD_LAUNCH(h, "sts_up");
   }
   return CPD_OK;
