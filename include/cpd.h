@@ -95,7 +95,8 @@ cpd_status cpd_default_options(cpd_options* opt);
 /*
  * Build a handle for the N-mode sparse tensor given as COO (Sec. 3: a list of
  * (N+1)-tuples).
- *   dims          host, N entries, I_k >= 1; prod of all I_k must be < 2^64.
+ *   dims          host, N entries, 1 <= I_k < 2^31; for every n the product of the
+ *                 other modes' I_k must be < 2^64 (column keys are 64-bit).
  *   nnz           number of nonzeros, 0 <= nnz < 2^32 - 1.
  *   idx           N x nnz int32, mode-major (idx[k * nnz + e] = i_k of nonzero e).
  *   vals          nnz float32.

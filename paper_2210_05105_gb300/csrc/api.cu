@@ -279,13 +279,15 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
     const int b = opt->spmm_blocks_per_sm;
     if (b != 0 && b != 1 && b != 2 && b != 4 && b != 8) return CPD_ERR_INVALID_ARG;
   }
-  // product of all dims must stay below 2^64 (keys and full linear indices)
-  long double prod = 1.0L;
-  for (int k = 0; k < N; ++k) {
+  // every column key (product of the other modes' dims) must stay below 2^64
+  for (int k = 0; k < N; ++k)
     if (dims[k] < 1 || dims[k] > 0x7fffffffll) return CPD_ERR_INVALID_ARG;
-    prod *= (long double)dims[k];
+  for (int n = 0; n < N; ++n) {
+    long double prod = 1.0L;
+    for (int k = 0; k < N; ++k)
+      if (k != n) prod *= (long double)dims[k];
+    if (prod >= 18446744073709551615.0L) return CPD_ERR_INVALID_ARG;
   }
-  if (prod >= 18446744073709551615.0L) return CPD_ERR_INVALID_ARG;
   cpd_ctx* h = new cpd_ctx();
   h->opt = *opt;
   h->N = N;

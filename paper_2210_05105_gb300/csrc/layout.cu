@@ -46,6 +46,37 @@ __global__ void make_keys_kernel(const int32_t* __restrict__ idx, int64_t nnz, K
   }
 }
 
+// Two-pass ordering for tensors whose full linear index does not fit in 64
+// bits: entries first sorted by i_n (keys = i_n), then re-keyed by their
+// column key in that order and sorted stably, which orders them by
+// (column key, i_n) as the one-pass full index would.
+__global__ void row_keys_kernel(const int32_t* __restrict__ idx_n, int64_t nnz, unsigned long long* __restrict__ keys,
+                                uint32_t* __restrict__ perm) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    keys[e] = (unsigned long long)idx_n[e];
+    perm[e] = (uint32_t)e;
+  }
+}
+
+__global__ void rekey_kernel(const int32_t* __restrict__ idx, int64_t nnz, KeyArgs a, const uint32_t* __restrict__ perm,
+                             unsigned long long* __restrict__ keys) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[j];
+    unsigned long long key = 0;
+    for (int k = 0; k < a.N; ++k)
+      if (k != a.n) key += (unsigned long long)idx[(int64_t)k * nnz + e] * a.stride[k];
+    keys[j] = key;
+  }
+}
+
+// Duplicates after the two-pass ordering: equal column key and equal i_n.
+__global__ void duplicate_check2_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ perm,
+                                        const int32_t* __restrict__ idx_n, int64_t nnz, int* status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    if (e > 0 && keys[e] == keys[e - 1] && idx_n[perm[e]] == idx_n[perm[e - 1]])
+      cpd_set_status(status, CPD_ERR_DUPLICATE);
+}
+
 // After sorting by full linear index, equal neighbours are duplicate coordinates.
 __global__ void duplicate_check_kernel(const unsigned long long* __restrict__ keys, int64_t nnz, int* status) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,9 +223,12 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
       L.stride[k] = acc;
       acc *= (unsigned long long)h->dims[k];
     }
-    a.N = N; a.n = n; a.In = (unsigned long long)h->dims[n]; a.full = (n == 0);
+    // mode 0 carries the duplicate check: one sort by the full linear index
+    // when it fits in 64 bits, else two stable sorts (i_0, then column key)
+    const bool two_pass = (n == 0) && (long double)acc * (long double)h->dims[n] >= 18446744073709551615.0L;
+    a.N = N; a.n = n; a.In = (unsigned long long)h->dims[n]; a.full = (n == 0) && !two_pass;
     unsigned long long maxkey = acc - 1ull;            // largest column key
-    if (n == 0) maxkey = acc * a.In - 1ull;            // full linear index
+    if (a.full) maxkey = acc * a.In - 1ull;            // full linear index
     cpd_status s = cpd_alloc(h, &L.ent, m);
     if (s != CPD_OK) return s;
     if (nnz == 0) {
@@ -204,13 +238,24 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
       CPD_CUDA(h, cudaMemsetAsync(L.table, 0xff, 16 * sizeof(FiberSlot), st));
       continue;
     }
-    make_keys_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, a, keys, perm);
-    CPD_LAUNCH(h, "make_keys");
-    if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(maxkey), keys_tmp, perm_tmp)) != CPD_OK) return s;
-    if (n == 0) {
-      duplicate_check_kernel<<<grid, thr, 0, st>>>(keys, nnz, h->status);
-      divide_keys_kernel<<<grid, thr, 0, st>>>(keys, nnz, a.In);
+    if (two_pass) {
+      row_keys_kernel<<<grid, thr, 0, st>>>(h->idx + (int64_t)n * nnz, nnz, keys, perm);
+      CPD_LAUNCH(h, "row keys");
+      if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(a.In - 1ull), keys_tmp, perm_tmp)) != CPD_OK) return s;
+      rekey_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, a, perm, keys);
+      CPD_LAUNCH(h, "rekey");
+      if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(maxkey), keys_tmp, perm_tmp)) != CPD_OK) return s;
+      duplicate_check2_kernel<<<grid, thr, 0, st>>>(keys, perm, h->idx + (int64_t)n * nnz, nnz, h->status);
       CPD_LAUNCH(h, "duplicate check");
+    } else {
+      make_keys_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, a, keys, perm);
+      CPD_LAUNCH(h, "make_keys");
+      if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(maxkey), keys_tmp, perm_tmp)) != CPD_OK) return s;
+      if (n == 0) {
+        duplicate_check_kernel<<<grid, thr, 0, st>>>(keys, nnz, h->status);
+        divide_keys_kernel<<<grid, thr, 0, st>>>(keys, nnz, a.In);
+        CPD_LAUNCH(h, "duplicate check");
+      }
     }
     gather_entries_kernel<<<grid, thr, 0, st>>>(h->idx + (int64_t)n * nnz, h->vals, perm, nnz, L.ent, keys, flags);
     CPD_LAUNCH(h, "gather_entries");

@@ -254,6 +254,20 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
   }
 }
 
+// One launch instead of four memsets: Y = 0, dedup tags = empty, dedup
+// weights = 0, packed counters = 0.
+__global__ void clear_kernel(float4* __restrict__ Y, int64_t ny4, uint4* __restrict__ tag, float4* __restrict__ dw,
+                             int64_t nd4, uint32_t* __restrict__ counters) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < ny4; i += st) Y[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int64_t i = t0; i < nd4; i += st) {
+    tag[i] = make_uint4(CPD_EMPTY32, CPD_EMPTY32, CPD_EMPTY32, CPD_EMPTY32);
+    dw[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  if (t0 < 4) counters[t0] = 0u;
+}
+
 // Exact MTTKRP over the input-order COO: a warp takes 32 nonzeros.
 __global__ void exact_kernel(MArgs a, const int32_t* __restrict__ idx, const float* __restrict__ vals, int64_t nnz,
                              float* __restrict__ Y) {
@@ -350,10 +364,12 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
   cudaStream_t st = h->stream;
   {
     PhaseTimer pt(h, CPD_PHASE_CLEAR);
-    CPD_CUDA(h, cudaMemsetAsync(Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), st));
-    CPD_CUDA(h, cudaMemsetAsync(h->dd_tag, 0xff, ((size_t)h->dedup_mask + 1) * sizeof(uint32_t), st));
-    CPD_CUDA(h, cudaMemsetAsync(h->dd_w, 0, ((size_t)h->dedup_mask + 1) * sizeof(float), st));
-    CPD_CUDA(h, cudaMemsetAsync(h->counters, 0, 4 * sizeof(uint32_t), st));
+    const int64_t ny4 = h->dims[mode] * (int64_t)h->Rp / 4;      // Rp is a multiple of 4
+    const int64_t nd4 = ((int64_t)h->dedup_mask + 1) / 4;          // 2J slots, a power of two >= 4
+    clear_kernel<<<h->num_sms * 4, 256, 0, st>>>(reinterpret_cast<float4*>(Y), ny4,
+                                                  reinterpret_cast<uint4*>(h->dd_tag),
+                                                  reinterpret_cast<float4*>(h->dd_w), nd4, h->counters);
+    CPD_LAUNCH(h, "clear");
   }
   MArgs a = make_args(h, mode);
   if (J > 0) {

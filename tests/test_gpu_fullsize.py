@@ -4,7 +4,9 @@ nonzeros, R = 32, J = 65,536, CP-ARLS-LEV, after two captured ALS rounds.
 
 * every one of the 65,536 draws of two mode updates equals the FP64
   oracle's inverse-CDF draw from the same factors (ties at 1e-12 C excepted),
-  with probabilities to 1e-12 relative;
+  with probabilities to 1e-10 relative: after two rounds the factor Grams have
+  condition numbers near 2e3, and the df64 pseudo-inverse is accurate to
+  ~cond * 2^-48 ~ 1e-11 per factor (5.8e-12 observed);
 * the downsampled MTTKRP of a full draw equals the oracle's over all 1e5 rows
   (relative Frobenius 1e-5) and selects the same nonzeros;
 * the solve and renormalisation equal the oracle's for that Y.
@@ -53,7 +55,7 @@ def test_fullsize_draws_equal_oracle(full):
         mism = np.any(gi != oi, axis=0)
         assert not np.any(mism & ~near), "draw differs away from a tie"
         ok = ~mism
-        assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-12
+        assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-10
 
 
 def test_fullsize_sampled_mttkrp_and_solve(full):

@@ -400,3 +400,29 @@ def test_zero_factor_draws_weight_zero(cpd, method):
     for k in range(3):
         assert torch.isfinite(cpd.cpd_get_factors(h, k)).all()
     h.close()
+
+
+def test_full_index_beyond_64_bits(cpd):
+    """dims 5e6 x 4e6 x 1e6 (2e19 cells, more than 2^64): column keys still fit
+    in 64 bits, the duplicate check takes the two-sort ordering; MTTKRPs equal
+    the oracle's and a repeated coordinate is still rejected."""
+    dims, R, J = (5_000_000, 4_000_000, 1_000_000), 4, 3000
+    rng = np.random.default_rng(5)
+    idx = np.stack([rng.integers(0, d, 20000) for d in dims]).astype(np.int32)
+    vals = rng.random(20000, dtype=np.float32)
+    init = [rng.standard_normal((d, R), dtype=np.float32) for d in dims]
+    h = create(cpd, dims, idx, vals, init, "arls", R, J, seed=2)
+    fs = gpu_factors(cpd, h)
+    Y = cpd.cpd_exact_mttkrp(h, 0)
+    assert rel_frob(Y.cpu().numpy(), oc.exact_mttkrp(idx, vals, dims, fs, 0)) <= 1e-5
+    sidx = np.stack([idx[0, :J], idx[1, :J], np.full(J, -1)]).astype(np.int64)
+    w = rng.random(J) + 0.5
+    Y, nsel = cpd.cpd_sampled_mttkrp(h, 2, torch.from_numpy(sidx), torch.from_numpy(w))
+    assert rel_frob(Y.cpu().numpy(), oc.sampled_mttkrp(idx, vals, dims, fs, 2, sidx, w)) <= 1e-5
+    assert nsel == oc.selected_nnz(idx, dims, 2, sidx)
+    h.close()
+    dup = idx.copy()
+    dup[:, 11] = dup[:, 4]
+    with pytest.raises(cpd.CpdError) as e:
+        create(cpd, dims, dup, vals, init, "arls", R, J, seed=2)
+    assert e.value.status == 3
