@@ -37,6 +37,7 @@ struct ModeLayout {
   // SpMM accumulates them in shared memory before one flush per block.
   int32_t* hot_rows = nullptr;
   int n_hot = 0;
+  uint32_t* row_code = nullptr;   // I_n: CPD_HOT_BIT | slot for hot rows, else the row's nonzero count
 };
 #define CPD_HOT_BIT 0x80000000u
 constexpr int CPD_HOT_MIN_COUNT = 256;   // a row with fewer nonzeros stays in the global path

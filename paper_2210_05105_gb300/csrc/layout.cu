@@ -283,7 +283,8 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
     if (h->hot_cap > 0) {
       const int64_t In = h->dims[n];
       uint32_t* counts = nullptr;
-      CPD_CUDA(h, cudaMallocAsync((void**)&counts, (size_t)In * 4, st));
+      if ((s = cpd_alloc(h, &counts, (size_t)In)) != CPD_OK) return s;
+      L.row_code = counts;
       CPD_CUDA(h, cudaMemsetAsync(counts, 0, (size_t)In * 4, st));
       CPD_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(uint32_t), st));    // candidate counter
       count_rows_kernel<<<grid, thr, 0, st>>>(L.ent, nnz, counts);
@@ -302,7 +303,6 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
         CPD_LAUNCH(h, "hot rows");
         L.n_hot = H;
       }
-      CPD_CUDA(h, cudaFreeAsync(counts, st));
     }
   }
   CPD_CUDA(h, cudaFreeAsync(keys, st));

@@ -36,6 +36,7 @@ struct MArgs {
   uint32_t uq_cap;
   const int32_t* hot_rows;   // row of each hot slot (entries carry CPD_HOT_BIT | slot)
   int n_hot;                 // hot slots accumulated in shared memory by this launch
+  const uint32_t* row_code;  // per row of mode n: CPD_HOT_BIT | slot for hot rows (exact MTTKRP)
 };
 
 __device__ __forceinline__ bool fiber_lookup(const FiberSlot* __restrict__ table, unsigned long long mask,
@@ -268,31 +269,77 @@ __global__ void clear_kernel(float4* __restrict__ Y, int64_t ny4, uint4* __restr
   if (t0 < 4) counters[t0] = 0u;
 }
 
-// Exact MTTKRP over the input-order COO: a warp takes 32 nonzeros.
-__global__ void exact_kernel(MArgs a, const int32_t* __restrict__ idx, const float* __restrict__ vals, int64_t nnz,
-                             float* __restrict__ Y) {
+// Exact MTTKRP (Eq. 6) over the input-order COO: a warp takes 32 nonzeros;
+// as in the sampled SpMM, C = Rp / 4 lanes cover one row with 16-byte
+// vectors (E = 32 / C nonzeros per warp instruction), the KRP row of a
+// nonzero is formed from its factor rows on the fly, and hot output rows
+// accumulate in shared memory before one flush per block.
+template <int NM>   // NM >= N: index registers per lane
+__global__ void __launch_bounds__(512, 2) exact_kernel(MArgs a, const int32_t* __restrict__ idx,
+                                                        const float* __restrict__ vals, int64_t nnz,
+                                                        float* __restrict__ Y) {
+  extern __shared__ float hot_acc[];
+  const int S = a.Rp + 1;
+  const int Hs = a.n_hot;
+  unsigned int* touched = reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * S);
+  for (int i = threadIdx.x; i < Hs * S; i += blockDim.x) hot_acc[i] = 0.0f;
+  for (int i = threadIdx.x; i < Hs; i += blockDim.x) touched[i] = 0u;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int C = a.Rp / 4;
+  const int E = C >= 32 ? 1 : 32 / C;
+  const int sub = C >= 32 ? 0 : lane / C;
+  const int q = C >= 32 ? lane : lane % C;
   for (int64_t c0 = warp * 32; c0 < nnz; c0 += nwarps * 32) {
     const int64_t e = c0 + lane;
-    int32_t ii[CPD_MAX_MODES];
+    int32_t ii[NM];
 #pragma unroll
-    for (int k = 0; k < CPD_MAX_MODES; ++k) ii[k] = (k < a.N && e < nnz) ? idx[(int64_t)k * nnz + e] : 0;
+    for (int k = 0; k < NM; ++k) ii[k] = (k < a.N && e < nnz) ? idx[(int64_t)k * nnz + e] : 0;
     const float v = e < nnz ? vals[e] : 0.0f;
     const int cnt = (int)(nnz - c0 < 32 ? nnz - c0 : 32);
-    for (int j = 0; j < cnt; ++j) {
-      const float vj = __shfl_sync(CPD_FULL, v, j);
-      int32_t ij[CPD_MAX_MODES];
+    for (int j0 = 0; j0 < cnt; j0 += E) {
+      const int jj = j0 + sub;
+      const int src = jj < 32 ? jj : 31;
+      int32_t ij[NM];
 #pragma unroll
-      for (int k = 0; k < CPD_MAX_MODES; ++k) ij[k] = __shfl_sync(CPD_FULL, ii[k], j);
-      for (int r = lane; r < a.R; r += 32) {
-        float m = vj;
-        for (int k = 0; k < a.N; ++k)
-          if (k != a.n) m *= a.U[k][(int64_t)ij[k] * a.Rp + r];
-        atomicAdd(Y + (int64_t)ij[a.n] * a.Rp + r, m);
+      for (int k = 0; k < NM; ++k) ij[k] = __shfl_sync(CPD_FULL, ii[k], src);
+      const float vj = __shfl_sync(CPD_FULL, v, src);
+      if (!(sub < E && jj < cnt)) continue;
+      float4 hv = make_float4(vj, vj, vj, vj);
+      for (int k = 0; k < a.N; ++k) {
+        if (k == a.n) continue;
+        const float4 u = reinterpret_cast<const float4*>(a.U[k] + (int64_t)ij[k] * a.Rp)[q];
+        hv.x *= u.x; hv.y *= u.y; hv.z *= u.z; hv.w *= u.w;
+      }
+      const uint32_t row = (uint32_t)ij[a.n];
+      const uint32_t code = a.row_code ? a.row_code[row] : 0u;
+      if ((code & CPD_HOT_BIT) && (int)(code & ~CPD_HOT_BIT) < Hs) {
+        const uint32_t slot = code & ~CPD_HOT_BIT;
+        float* acc = hot_acc + (size_t)slot * S + 4 * q;
+        atomicAdd(acc + 0, hv.x);
+        atomicAdd(acc + 1, hv.y);
+        atomicAdd(acc + 2, hv.z);
+        atomicAdd(acc + 3, hv.w);
+        touched[slot] = 1u;
+      } else {
+        float* yp = Y + (int64_t)row * a.Rp + 4 * q;
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(hv.x), "f"(hv.y), "f"(hv.z),
+                     "f"(hv.w)
+                     : "memory");
       }
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < Hs * C; i += blockDim.x) {
+    const int slot = i / C, qq = i - slot * C;
+    if (!touched[slot]) continue;
+    const float* acc = hot_acc + (size_t)slot * S + 4 * qq;
+    float* yp = Y + (int64_t)a.hot_rows[slot] * a.Rp + 4 * qq;
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[1]), "f"(acc[2]),
+                 "f"(acc[3])
+                 : "memory");
   }
 }
 
@@ -331,7 +378,11 @@ int cpd_spmm_hot_slots(int Rp, int bps) {
   return (int)(budget / ((size_t)(Rp + 1) * 4 + 4));
 }
 cpd_status cpd_spmm_init(cpd_ctx* h) {
-  return cpd_smem_attr(h, (const void*)spmm_kernel, (size_t)cpd_spmm_hot_slots(h->Rp, 1) * ((size_t)(h->Rp + 1) * 4 + 4));
+  const size_t shm = (size_t)cpd_spmm_hot_slots(h->Rp, 1) * ((size_t)(h->Rp + 1) * 4 + 4);
+  const cpd_status s = cpd_smem_attr(h, (const void*)spmm_kernel, shm);
+  if (s != CPD_OK) return s;
+  const cpd_status s4 = cpd_smem_attr(h, (const void*)exact_kernel<4>, shm);
+  return s4 != CPD_OK ? s4 : cpd_smem_attr(h, (const void*)exact_kernel<CPD_MAX_MODES>, shm);
 }
 
 namespace {
@@ -409,7 +460,15 @@ cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y) {
   CPD_CUDA(h, cudaMemsetAsync(Y, 0, (size_t)h->dims[mode] * h->Rp * sizeof(float), st));
   if (h->nnz == 0) return CPD_OK;
   MArgs a = make_args(h, mode);
-  exact_kernel<<<h->num_sms * 8, 256, 0, st>>>(a, h->idx, h->vals, h->nnz, Y);
+  const int bps = 2;   // two 512-thread blocks per SM (64 registers a thread)
+  a.n_hot = h->mode[mode].row_code ? std::min(h->mode[mode].n_hot, cpd_spmm_hot_slots(h->Rp, bps)) : 0;
+  a.hot_rows = h->mode[mode].hot_rows;
+  a.row_code = h->mode[mode].row_code;
+  const size_t shm = (size_t)a.n_hot * ((size_t)(h->Rp + 1) * 4 + 4);
+  if (h->N <= 4)
+    exact_kernel<4><<<h->num_sms * bps, 512, shm, st>>>(a, h->idx, h->vals, h->nnz, Y);
+  else
+    exact_kernel<CPD_MAX_MODES><<<h->num_sms * bps, 512, shm, st>>>(a, h->idx, h->vals, h->nnz, Y);
   CPD_LAUNCH(h, "exact_mttkrp");
   return CPD_OK;
 }
