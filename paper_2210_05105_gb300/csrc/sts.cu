@@ -74,6 +74,21 @@ __global__ void sts_up_kernel(float* __restrict__ tree, int64_t lo, int nstride)
   }
 }
 
+// The upper levels [1, 2 lo) in one block, level by level (they are small;
+// one launch instead of log2(lo) + 1).
+__global__ void sts_up_top_kernel(float* __restrict__ tree, int64_t lo, int nstride) {
+  float4* t4 = reinterpret_cast<float4*>(tree);
+  const int q4 = nstride / 4;
+  for (int64_t l = lo; l >= 1; l >>= 1) {
+    for (int64_t e = threadIdx.x; e < l * q4; e += blockDim.x) {
+      const int64_t v = l + e / q4, q = e % q4;
+      const float4 x = t4[(2 * v) * q4 + q], y = t4[(2 * v + 1) * q4 + q];
+      t4[v * q4 + q] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+    }
+    __syncthreads();
+  }
+}
+
 struct GgtArgs {
   const double* G[CPD_MAX_MODES];
   double* out[CPD_MAX_MODES];
@@ -445,11 +460,16 @@ cpd_status cpd_sts_refresh(cpd_ctx* h, int k) {
   const int grid = (int)std::min<int64_t>(nleaf, (int64_t)h->num_sms * 8);
   sts_leaf_kernel<<<grid, 256, (size_t)h->F * R * 4, h->stream>>>(h->U[k], I, R, h->Rp, h->F, L, nleaf, h->tree32[k]);
   CPD_LAUNCH(h, "sts_leaf");
-  for (int64_t lo = L / 2; lo >= 1; lo /= 2) {
+  int64_t lo = L / 2;
+  for (; lo > 64; lo /= 2) {
     const int64_t total = lo * nstride / 4;
     const int g = (int)std::min<int64_t>(cpd_ceil_div(total, 256), (int64_t)h->num_sms * 8);
     sts_up_kernel<<<g, 256, 0, h->stream>>>(h->tree32[k], lo, nstride);
     CPD_LAUNCH(h, "sts_up");
+  }
+  if (lo >= 1) {
+    sts_up_top_kernel<<<1, 1024, 0, h->stream>>>(h->tree32[k], lo, nstride);
+    CPD_LAUNCH(h, "sts_up_top");
   }
   return CPD_OK;
 }
