@@ -55,6 +55,13 @@ __global__ void bump_kernel(unsigned long long* ctr) { *ctr += 1ull; }
 cpd_status fork_pinv(cpd_ctx* h, int mode) {
   CPD_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
   CPD_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+  if (h->opt.method == CPD_ARLS_LEV) {
+    // the mode's MTTKRP buffers are cleared on the branch too (the previous
+    // solve has consumed Y); the main branch waits for it before the probe
+    cpd_status sc = cpd_clear_launch(h, mode, h->Y, h->side_stream);
+    if (sc != CPD_OK) return sc;
+    CPD_CUDA(h, cudaEventRecord(h->ev_clear, h->side_stream));
+  }
   cudaStream_t main = h->stream;
   h->stream = h->side_stream;
   cpd_status s = cpd_hadamard_pinv(h, mode, h->Gn, h->Gnpinv, h->pinv_scratch2);
@@ -74,7 +81,8 @@ cpd_status mode_update(cpd_ctx* h, int n, bool forked = false) {
   } else {
     const int64_t J = h->opt.samples;
     if ((s = cpd_draw(h, n, J, h->sweep_ctr, 0, h->samp_idx, h->samp_p, h->samp_w)) != CPD_OK) return s;
-    if ((s = cpd_sampled_mttkrp_launch(h, n, h->samp_idx, h->samp_w, h->samp_p, J, h->Y, nullptr)) != CPD_OK)
+    cudaEvent_t cleared = (forked && h->opt.method == CPD_ARLS_LEV) ? h->ev_clear : nullptr;
+    if ((s = cpd_sampled_mttkrp_launch(h, n, h->samp_idx, h->samp_w, h->samp_p, J, h->Y, nullptr, cleared)) != CPD_OK)
       return s;
   }
   if (forked) CPD_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
@@ -302,7 +310,8 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_clear, cudaEventDisableTiming) != cudaSuccess) {
     g_create_error = "stream or event creation failed";
     cpd_destroy(h);
     return CPD_ERR_CUDA;
@@ -507,6 +516,7 @@ void cpd_destroy(cpd_handle h) {
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_clear) cudaEventDestroy(h->ev_clear);
   delete h;
 }
 

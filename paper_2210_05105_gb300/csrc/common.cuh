@@ -52,6 +52,7 @@ struct cpd_ctx {
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture the sweep graph
   cudaStream_t side_stream = nullptr; // forked branch of the captured sweep
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_clear = nullptr;     // the forked branch has cleared the next MTTKRP's buffers
   double* pinv_scratch2 = nullptr;    // 2 R^2: scratch of the forked pseudo-inverse
   int device = 0, num_sms = 0;
   std::string last_error;
@@ -302,8 +303,9 @@ cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double*
 cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d_sweep,
                     unsigned long long sweep, int32_t* out_idx, double* out_p, double* out_w);
 // mttkrp.cu
+cpd_status cpd_clear_launch(cpd_ctx* h, int mode, float* Y, cudaStream_t st);
 cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, const double* w,
-                                     const double* p, int64_t J, float* Y, int64_t* out_nnz_sel);
+                                     const double* p, int64_t J, float* Y, int64_t* out_nnz_sel, cudaEvent_t cleared = nullptr);
 cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y);
 // scan.cu
 cpd_status cpd_scan_u32(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);

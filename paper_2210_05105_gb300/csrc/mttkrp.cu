@@ -409,18 +409,27 @@ MArgs make_args(cpd_ctx* h, int mode) {
 }  // namespace
 
 // Y (I_mode x Rp, internal stride) := mat(T, mode) S^T S U_{!=mode}.
+// Y = 0 (rows of `mode`), dedup tables empty, counters 0, on stream st.
+cpd_status cpd_clear_launch(cpd_ctx* h, int mode, float* Y, cudaStream_t st) {
+  const int64_t ny4 = h->dims[mode] * (int64_t)h->Rp / 4;      // Rp is a multiple of 4
+  const int64_t nd4 = ((int64_t)h->dedup_mask + 1) / 4;          // 2J slots, a power of two >= 4
+  clear_kernel<<<h->num_sms * 4, 256, 0, st>>>(reinterpret_cast<float4*>(Y), ny4,
+                                                reinterpret_cast<uint4*>(h->dd_tag),
+                                                reinterpret_cast<float4*>(h->dd_w), nd4, h->counters);
+  CPD_LAUNCH(h, "clear");
+  return CPD_OK;
+}
+
 cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, const double* w, const double* p,
-                                     int64_t J, float* Y, int64_t* out_nnz_sel) {
+                                     int64_t J, float* Y, int64_t* out_nnz_sel, cudaEvent_t cleared) {
   (void)p;
   cudaStream_t st = h->stream;
-  {
+  if (cleared) {
+    CPD_CUDA(h, cudaStreamWaitEvent(st, cleared, 0));     // cleared on the forked branch
+  } else {
     PhaseTimer pt(h, CPD_PHASE_CLEAR);
-    const int64_t ny4 = h->dims[mode] * (int64_t)h->Rp / 4;      // Rp is a multiple of 4
-    const int64_t nd4 = ((int64_t)h->dedup_mask + 1) / 4;          // 2J slots, a power of two >= 4
-    clear_kernel<<<h->num_sms * 4, 256, 0, st>>>(reinterpret_cast<float4*>(Y), ny4,
-                                                  reinterpret_cast<uint4*>(h->dd_tag),
-                                                  reinterpret_cast<float4*>(h->dd_w), nd4, h->counters);
-    CPD_LAUNCH(h, "clear");
+    const cpd_status s = cpd_clear_launch(h, mode, Y, st);
+    if (s != CPD_OK) return s;
   }
   MArgs a = make_args(h, mode);
   if (J > 0) {
