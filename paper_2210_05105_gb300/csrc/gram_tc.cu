@@ -30,6 +30,7 @@ constexpr int GT_TK = 64;            // rows of U per tile (the MMA K of one sta
 constexpr int GT_THREADS = 256;
 constexpr uint32_t GT_KC = GT_TK / 8;        // core matrices along K per tile
 constexpr uint32_t GT_SBO = GT_KC * 128;     // bytes between 8-row groups
+constexpr int GT_MAXW = 2;                   // work items per thread: Rp * GT_KC <= 512 (Rp <= 64)
 constexpr long long GT_WAIT_CYCLES = 4000000000ll;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -107,16 +108,39 @@ __global__ void __launch_bounds__(GT_THREADS)
   const uint32_t base = smem_u32(gsm);
   const int64_t ntiles = (I + GT_TK - 1) / GT_TK;
 
+  // the thread's work items (column r, 8-row group kg) of a tile: at most
+  // GT_MAXW; the next tile's values are loaded while the current one is
+  // split and stored (register double buffering hides the load latency)
+  const int nwork = Rp * (int)GT_KC;
+  float cur[GT_MAXW][8], nxt[GT_MAXW][8];
+  auto load_tile = [&](int64_t tl, float (&dst)[GT_MAXW][8]) {
+#pragma unroll
+    for (int wi = 0; wi < GT_MAXW; ++wi) {
+      const int w = t + wi * GT_THREADS;
+      const int r = w % Rp, kg = w / Rp;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t k = tl * GT_TK + kg * 8 + j;
+        dst[wi][j] = (w < nwork && k < I && r < R) ? Uin[k * Rp + r] : 0.0f;
+      }
+    }
+  };
+  if ((int64_t)blockIdx.x < ntiles) load_tile(blockIdx.x, cur);
+
   int it = 0;
   bool aborted = false;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int b = it & 1;
+    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x, nxt);
     bool ok = true;
     if (it >= 2) ok = gt_wait(smem_u32(&mbar[b]), (uint32_t)((it - 2) >> 1) & 1u);   // MMAs of tile it-2 read buffer b
     if (__syncthreads_or(!ok)) { aborted = true; break; }
     unsigned char* buf = gsm + (size_t)b * buf_bytes;
     const int64_t k0 = tile * GT_TK;
-    for (int w = t; w < Rp * (int)GT_KC; w += GT_THREADS) {
+#pragma unroll
+    for (int wi = 0; wi < GT_MAXW; ++wi) {
+      const int w = t + wi * GT_THREADS;
+      if (w >= nwork) continue;
       const int r = w % Rp, kg = w / Rp;
       uint32_t ph[4], pm[4], pl[4];
 #pragma unroll
@@ -125,11 +149,8 @@ __global__ void __launch_bounds__(GT_THREADS)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int64_t k = k0 + kg * 8 + j + q;
-          float x = 0.0f;
-          if (k < I) {
-            if (r < R) x = Uin[k * Rp + r] * inv[r];
-            if (write_back) Uout[k * Rp + r] = x;
-          }
+          const float x = cur[wi][j + q] * inv[r];
+          if (write_back && k < I) Uout[k * Rp + r] = x;
           v[q] = x;
         }
         __nv_bfloat16 hi[2], mi[2], lo[2];
@@ -155,6 +176,10 @@ __global__ void __launch_bounds__(GT_THREADS)
         *reinterpret_cast<uint4*>(buf + ((uint32_t)(m >> 3) * GT_KC + (uint32_t)kg) * 128u + (uint32_t)(m & 7) * 16u) = val;
       }
     }
+#pragma unroll
+    for (int wi = 0; wi < GT_MAXW; ++wi)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cur[wi][j] = nxt[wi][j];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // generic-proxy stores -> tensor core
     __syncthreads();
     if (t == 0) {

@@ -200,46 +200,40 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
     const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
     // C lanes cover one row of Rp floats (C <= 32 since R <= 128) with
     // 16-byte vector reductions, so one warp instruction updates E = 32 / C
-    // selected nonzeros at once.  Two such groups are in flight per lane:
-    // their KRP-row loads are issued before either of their reductions.
+    // selected nonzeros at once.  Consecutive positions of a lane group
+    // mostly belong to the same drawn column, so its KRP row is kept in
+    // registers and loaded again only when the column changes.
     const float4* H4 = reinterpret_cast<const float4*>(a.H);
-    for (int j0 = 0; j0 < cnt; j0 += 2 * E) {
-      float4 hv[2];
-      float sj[2];
-      uint32_t rj[2];
-      bool act[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int jj = j0 + u * E + sub;
-        const int src = jj < 32 ? jj : 31;
-        rj[u] = __shfl_sync(CPD_FULL, row, src);
-        sj[u] = __shfl_sync(CPD_FULL, scale, src);
-        const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
-        act[u] = sub < E && jj < cnt;
-        hv[u] = act[u] ? H4[(int64_t)uj * C + q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    uint32_t cu = 0xffffffffu;
+    float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int j0 = 0; j0 < cnt; j0 += E) {
+      const int jj = j0 + sub;
+      const int src = jj < 32 ? jj : 31;
+      uint32_t r = __shfl_sync(CPD_FULL, row, src);
+      const float sj = __shfl_sync(CPD_FULL, scale, src);
+      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
+      if (!(sub < E && jj < cnt)) continue;
+      if (uj != cu) {
+        hv = H4[(int64_t)uj * C + q];
+        cu = uj;
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        if (!act[u]) continue;
-        uint32_t r = rj[u];
-        if (r & CPD_HOT_BIT) {
-          const uint32_t slot = r & ~CPD_HOT_BIT;
-          if ((int)slot < Hs) {
-            float* acc = hot_acc + (size_t)slot * S + 4 * q;
-            atomicAdd(acc + 0, sj[u] * hv[u].x);
-            atomicAdd(acc + 1, sj[u] * hv[u].y);
-            atomicAdd(acc + 2, sj[u] * hv[u].z);
-            atomicAdd(acc + 3, sj[u] * hv[u].w);
-            touched[slot] = 1u;
-            continue;
-          }
-          r = (uint32_t)a.hot_rows[slot];
+      if (r & CPD_HOT_BIT) {
+        const uint32_t slot = r & ~CPD_HOT_BIT;
+        if ((int)slot < Hs) {
+          float* acc = hot_acc + (size_t)slot * S + 4 * q;
+          atomicAdd(acc + 0, sj * hv.x);
+          atomicAdd(acc + 1, sj * hv.y);
+          atomicAdd(acc + 2, sj * hv.z);
+          atomicAdd(acc + 3, sj * hv.w);
+          touched[slot] = 1u;
+          continue;
         }
-        float* yp = Y + (int64_t)r * a.Rp + 4 * q;
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj[u] * hv[u].x),
-                     "f"(sj[u] * hv[u].y), "f"(sj[u] * hv[u].z), "f"(sj[u] * hv[u].w)
-                     : "memory");
+        r = (uint32_t)a.hot_rows[slot];
       }
+      float* yp = Y + (int64_t)r * a.Rp + 4 * q;
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj * hv.x), "f"(sj * hv.y),
+                   "f"(sj * hv.z), "f"(sj * hv.w)
+                   : "memory");
     }
   }
   // flush the block's hot rows that it touched
