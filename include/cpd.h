@@ -86,7 +86,10 @@ typedef struct {
                               {1, 2, 4, 8}, each holding an equal share of the SM's
                               shared memory for hot-row accumulation; 0 = default
                               (2); cpd_autotune may change it */
-  int32_t reserved_i32[5];
+  int32_t duplicate_policy; /* repeated COO coordinates: 0 = rejected with
+                              CPD_ERR_DUPLICATE; 1 = their values are summed into one
+                              nonzero (the handle then holds fewer nonzeros) */
+  int32_t reserved_i32[4];
 } cpd_options;
 
 /* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */

@@ -30,7 +30,7 @@ class cpd_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("leaf_rows", ctypes.c_int32), ("input_on_host", ctypes.c_int32),
                 ("reserved_i64", ctypes.c_int64 * 4), ("sketched_gram", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("spmm_blocks_per_sm", ctypes.c_int32),
-                ("reserved_i32", ctypes.c_int32 * 5)]
+                ("duplicate_policy", ctypes.c_int32), ("reserved_i32", ctypes.c_int32 * 4)]
 
 
 class CpdError(RuntimeError):
@@ -114,7 +114,7 @@ class Handle:
 
 
 def cpd_create(dims, idx, vals, init_factors, method="arls", rank=8, samples=2000, seed=0, leaf_rows=0,
-               stream=None, sketched_gram=False, fast=False, spmm_blocks_per_sm=0):
+               stream=None, sketched_gram=False, fast=False, spmm_blocks_per_sm=0, sum_duplicates=False):
     """Build a handle.  idx (N, nnz) int32, vals (nnz,) float32 and the init
     factors (list of (I_k, R) float32) must all be on the same device: all
     CUDA, or all CPU (then they are copied by the library, host input)."""
@@ -138,6 +138,7 @@ def cpd_create(dims, idx, vals, init_factors, method="arls", rank=8, samples=200
     opt.sketched_gram = 1 if sketched_gram else 0
     opt.precision = 1 if fast else 0
     opt.spmm_blocks_per_sm = int(spmm_blocks_per_sm)
+    opt.duplicate_policy = 1 if sum_duplicates else 0
     dims_arr = (ctypes.c_int64 * N)(*dims)
     if stream is None and torch.cuda.is_available():
         stream = torch.cuda.current_stream()

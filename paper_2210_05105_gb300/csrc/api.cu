@@ -287,6 +287,7 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
     const int b = opt->spmm_blocks_per_sm;
     if (b != 0 && b != 1 && b != 2 && b != 4 && b != 8) return CPD_ERR_INVALID_ARG;
   }
+  if (opt->duplicate_policy != 0 && opt->duplicate_policy != 1) return CPD_ERR_INVALID_ARG;
   // every column key (product of the other modes' dims) must stay below 2^64
   for (int k = 0; k < N; ++k)
     if (dims[k] < 1 || dims[k] > 0x7fffffffll) return CPD_ERR_INVALID_ARG;

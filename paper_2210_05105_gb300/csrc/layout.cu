@@ -77,6 +77,35 @@ __global__ void duplicate_check2_kernel(const unsigned long long* __restrict__ k
       cpd_set_status(status, CPD_ERR_DUPLICATE);
 }
 
+// Summing duplicates (duplicate_policy 1): after the mode-0 ordering, run
+// heads (first entry of each distinct coordinate) ...
+__global__ void run_heads_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ perm,
+                                 const int32_t* __restrict__ idx0, int64_t nnz, int two_pass,
+                                 uint32_t* __restrict__ head) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    bool same = e > 0 && keys[e] == keys[e - 1];
+    if (same && two_pass) same = idx0[perm[e]] == idx0[perm[e - 1]];
+    head[e] = same ? 0u : 1u;
+  }
+}
+
+// ... and one thread per run writes the coordinate and the sum of its values
+// (in sorted order, so the result is deterministic) to the run's slot.
+__global__ void run_sum_kernel(const uint32_t* __restrict__ head, const uint32_t* __restrict__ rid,
+                               const uint32_t* __restrict__ perm, const int32_t* __restrict__ idx,
+                               const float* __restrict__ vals, int64_t nnz, int N, int64_t nu,
+                               int32_t* __restrict__ idx_out, float* __restrict__ vals_out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    if (!head[e]) continue;
+    const int64_t r = rid[e];
+    const int64_t p = perm[e];
+    for (int k = 0; k < N; ++k) idx_out[(int64_t)k * nu + r] = idx[(int64_t)k * nnz + p];
+    float s = vals[p];
+    for (int64_t f = e + 1; f < nnz && !head[f]; ++f) s += vals[perm[f]];
+    vals_out[r] = s;
+  }
+}
+
 // After sorting by full linear index, equal neighbours are duplicate coordinates.
 __global__ void duplicate_check_kernel(const unsigned long long* __restrict__ keys, int64_t nnz, int* status) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -181,7 +210,7 @@ int bits_for(unsigned long long maxval) {
 }  // namespace
 
 cpd_status cpd_build_layouts(cpd_ctx* h) {
-  const int64_t nnz = h->nnz;
+  int64_t nnz = h->nnz;
   const int N = h->N;
   cudaStream_t st = h->stream;
   const int grid = h->num_sms * 8, thr = 256;
@@ -211,6 +240,50 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
   CPD_CUDA(h, cudaMallocAsync((void**)&perm_tmp, m * 4, st));
   CPD_CUDA(h, cudaMallocAsync((void**)&flags, m * 4, st));
   CPD_CUDA(h, cudaMallocAsync((void**)&fid, m * 4, st));
+
+  // duplicate_policy 1: order by coordinate once, sum repeated coordinates
+  // into a compacted COO, then build every layout from it
+  if (h->opt.duplicate_policy == 1 && nnz > 1) {
+    KeyArgs a;
+    unsigned long long acc = 1;
+    for (int k = 0; k < CPD_MAX_MODES; ++k) a.stride[k] = 0;
+    for (int k = 1; k < N; ++k) { a.stride[k] = acc; acc *= (unsigned long long)h->dims[k]; }
+    const bool two_pass = (long double)acc * (long double)h->dims[0] >= 18446744073709551615.0L;
+    a.N = N; a.n = 0; a.In = (unsigned long long)h->dims[0]; a.full = !two_pass;
+    cpd_status s;
+    if (two_pass) {
+      row_keys_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, keys, perm);
+      if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(a.In - 1ull), keys_tmp, perm_tmp)) != CPD_OK) return s;
+      rekey_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, a, perm, keys);
+      if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(acc - 1ull), keys_tmp, perm_tmp)) != CPD_OK) return s;
+    } else {
+      make_keys_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, a, keys, perm);
+      if ((s = cpd_radix_sort_u64(h, keys, perm, nnz, bits_for(acc * a.In - 1ull), keys_tmp, perm_tmp)) != CPD_OK)
+        return s;
+    }
+    run_heads_kernel<<<grid, thr, 0, st>>>(keys, perm, h->idx, nnz, two_pass ? 1 : 0, flags);
+    CPD_LAUNCH(h, "run heads");
+    uint32_t* d_total = (uint32_t*)keys_tmp;
+    if ((s = cpd_scan_u32(h, flags, fid, nnz, d_total)) != CPD_OK) return s;
+    uint32_t nu = 0;
+    CPD_CUDA(h, cudaMemcpyAsync(&nu, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CPD_CUDA(h, cudaStreamSynchronize(st));
+    if ((int64_t)nu < nnz) {
+      int32_t* idx2 = nullptr;
+      float* vals2 = nullptr;
+      if ((s = cpd_alloc(h, &idx2, (size_t)N * nu)) != CPD_OK) return s;
+      if ((s = cpd_alloc(h, &vals2, (size_t)nu)) != CPD_OK) return s;
+      run_sum_kernel<<<grid, thr, 0, st>>>(flags, fid, perm, h->idx, h->vals, nnz, N, nu, idx2, vals2);
+      CPD_LAUNCH(h, "run sums");
+      CPD_CUDA(h, cudaStreamSynchronize(st));
+      cpd_free(h, h->idx);
+      cpd_free(h, h->vals);
+      h->idx = idx2;
+      h->vals = vals2;
+      h->nnz = nu;
+      nnz = nu;
+    }
+  }
 
   for (int n = 0; n < N; ++n) {
     ModeLayout& L = h->mode[n];

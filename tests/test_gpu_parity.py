@@ -426,3 +426,37 @@ def test_full_index_beyond_64_bits(cpd):
     with pytest.raises(cpd.CpdError) as e:
         create(cpd, dims, dup, vals, init, "arls", R, J, seed=2)
     assert e.value.status == 3
+
+
+def test_duplicate_coordinates_summed_on_request(cpd):
+    """duplicate_policy = 1: repeated coordinates become one nonzero holding
+    the sum of their values (both in the 64-bit full-index ordering and in
+    the two-sort ordering of a tensor with more than 2^64 cells)."""
+    for dims in [(30, 20, 10), (5_000_000, 4_000_000, 1_000_000)]:
+        rng = np.random.default_rng(8)
+        base = np.stack([rng.integers(0, d, 3000) for d in dims]).astype(np.int32)
+        rep = base[:, rng.integers(0, 3000, 1500)]
+        idx = np.concatenate([base, rep], axis=1)
+        vals = rng.random(idx.shape[1], dtype=np.float32)
+        R, J = 4, 200
+        init = [rng.standard_normal((d, R), dtype=np.float32) for d in dims]
+        h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                           [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=1,
+                           sum_duplicates=True)
+        keys = [np.asarray(x, dtype=np.int64) for x in idx]
+        order = np.lexsort(keys[::-1])
+        srt = idx[:, order]
+        newrun = np.ones(srt.shape[1], dtype=bool)
+        newrun[1:] = np.any(srt[:, 1:] != srt[:, :-1], axis=0)
+        rid = np.cumsum(newrun) - 1
+        uidx = srt[:, newrun]
+        uvals = np.zeros(uidx.shape[1])
+        np.add.at(uvals, rid, vals[order].astype(np.float64))
+        fs = gpu_factors(cpd, h)
+        for mode in range(3):
+            Y = cpd.cpd_exact_mttkrp(h, mode)
+            assert rel_frob(Y.cpu().numpy(), oc.exact_mttkrp(uidx, uvals, dims, fs, mode)) <= 1e-5
+        f = cpd.cpd_fit(h)
+        fo = oc.fit(uidx, uvals, fs, cpd.cpd_get_sigma(h).cpu().numpy())
+        assert abs(f - fo) < 1e-9
+        h.close()
