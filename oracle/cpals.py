@@ -19,15 +19,18 @@ Conventions
   index of the lowest remaining mode varies fastest.  The row ("column of
   mat(T, n)") linear key is  key = sum_{k != n} i_k * prod_{k' < k, k' != n} I_k'.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
 * Moore-Penrose pseudo-inverse (Eq. 4): symmetric eigendecomposition,
   eigenvalues <= R * 2^-52 * lambda_max are treated as zero.
 * Sampling weight (Sec. 3.2, "extracts and reweights"): row j of S is
   e_{row_j}^T / sqrt(J p_j), so S^T S carries weight w_j = 1 / (J p_j) on row_j;
   draws are i.i.d. with replacement (Theorem 3.1).
 * Inverse-CDF draw (Algorithm 3, per factor): i = smallest index with
-  CDF[i] > u * C; if rounding puts u * C at or past CDF[I-1], the last row of
-  nonzero weight is taken.
+  CDF[i] > u * C; if rounding puts u * C at or past CDF[I-1], the first row
+  whose running sum reaches C (the last row whose bin has nonzero width).
+* A factor whose scores are all zero (C = 0) has no distribution; every KRP
+  row through it is zero, so its draws take row 0 with probability 0 and
+  weight 0.
 * STS-CP (Sec. 4.1, Algorithm 5): factors are drawn in ascending mode order
   (excluding n); G_{>k} = G^+ (*) Grams of the factors drawn after k; the walk
   keeps an absolute target t = u * m(root) and goes left iff t < m(left),
