@@ -155,6 +155,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   h->hot_cap = cpd_spmm_hot_slots(h->Rp, 1);
   if ((s = cpd_spmm_init(h)) != CPD_OK) return s;
   if ((s = cpd_build_layouts(h)) != CPD_OK) return s;
+  nnz = h->nnz;            // fewer when repeated coordinates were summed
 
   // ||T||^2
   h->gram_blocks = h->num_sms * 4;
