@@ -120,20 +120,32 @@ __global__ void divide_keys_kernel(unsigned long long* __restrict__ keys, int64_
   for (; e < nnz; e += st) keys[e] = keys[e] / In;
 }
 
-__global__ void gather_entries_kernel(const int32_t* __restrict__ idx_n, const float* __restrict__ vals,
-                                      const uint32_t* __restrict__ perm, int64_t nnz, uint2* __restrict__ ent,
-                                      const unsigned long long* __restrict__ keys, uint32_t* __restrict__ flags) {
+// (i_n, value) of every nonzero in input order, packed into 8 bytes, so that
+// the permuting gather below makes one random access per entry, not two.
+__global__ void pack_entries_kernel(const int32_t* __restrict__ idx_n, const float* __restrict__ vals, int64_t nnz,
+                                    uint2* __restrict__ packed) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    packed[e] = make_uint2((uint32_t)idx_n[e], __float_as_uint(vals[e]));
+}
+
+__global__ void gather_entries_kernel(const uint2* __restrict__ packed, const uint32_t* __restrict__ perm, int64_t nnz,
+                                      uint2* __restrict__ ent, const unsigned long long* __restrict__ keys,
+                                      uint32_t* __restrict__ flags) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t st = (int64_t)gridDim.x * blockDim.x;
   for (; e < nnz; e += st) {
-    uint32_t p = perm[e];
-    ent[e] = make_uint2((uint32_t)idx_n[p], __float_as_uint(vals[p]));
+    ent[e] = packed[perm[e]];
     flags[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1u : 0u;
   }
 }
 
-__global__ void count_rows_kernel(const uint2* __restrict__ ent, int64_t nnz, uint32_t* __restrict__ counts) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+// Row counts of every stride-th entry: hot rows only need to be recognised
+// (their slots order them by count), and counting every entry would send
+// millions of atomics to the same few Zipf-hot counters.
+__global__ void count_rows_kernel(const uint2* __restrict__ ent, int64_t nnz, int64_t stride,
+                                  uint32_t* __restrict__ counts) {
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x * stride)
     atomicAdd(&counts[ent[e].x], 1u);
 }
 
@@ -330,7 +342,9 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
         CPD_LAUNCH(h, "duplicate check");
       }
     }
-    gather_entries_kernel<<<grid, thr, 0, st>>>(h->idx + (int64_t)n * nnz, h->vals, perm, nnz, L.ent, keys, flags);
+    uint2* packed = reinterpret_cast<uint2*>(keys_tmp);   // sort scratch, free until the scan below
+    pack_entries_kernel<<<grid, thr, 0, st>>>(h->idx + (int64_t)n * nnz, h->vals, nnz, packed);
+    gather_entries_kernel<<<grid, thr, 0, st>>>(packed, perm, nnz, L.ent, keys, flags);
     CPD_LAUNCH(h, "gather_entries");
     uint32_t* d_total = (uint32_t*)keys_tmp;   // scratch word
     if ((s = cpd_scan_u32(h, flags, fid, nnz, d_total)) != CPD_OK) return s;
@@ -360,9 +374,11 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
       L.row_code = counts;
       CPD_CUDA(h, cudaMemsetAsync(counts, 0, (size_t)In * 4, st));
       CPD_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(uint32_t), st));    // candidate counter
-      count_rows_kernel<<<grid, thr, 0, st>>>(L.ent, nnz, counts);
+      const int64_t stride = std::max<int64_t>(1, nnz / (int64_t(1) << 22));   // about 4M counted entries
+      count_rows_kernel<<<grid, thr, 0, st>>>(L.ent, nnz, stride, counts);
+      const uint32_t min_count = (uint32_t)std::max<int64_t>(1, CPD_HOT_MIN_COUNT / stride);
       const unsigned rgrid = (unsigned)std::min<int64_t>(cpd_ceil_div(In, thr), (int64_t)h->num_sms * 8);
-      hot_candidates_kernel<<<rgrid, thr, 0, st>>>(counts, In, CPD_HOT_MIN_COUNT, keys, perm, flags);
+      hot_candidates_kernel<<<rgrid, thr, 0, st>>>(counts, In, min_count, keys, perm, flags);
       CPD_LAUNCH(h, "hot candidates");
       uint32_t ncand = 0;
       CPD_CUDA(h, cudaMemcpyAsync(&ncand, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
