@@ -304,30 +304,19 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
   __syncthreads();
   bool ok = false;
   for (int it = 0; it < max_newton && !ok; ++it) {
-    // W = I - G X with G X in df64; the thread's entries advance together
-    // (independent chains)
+    // W = I - G X with G X in df64
     float emax = 0.0f;
-    {
-      float ah[PINV_PER_T], al[PINV_PER_T];
-#pragma unroll
-      for (int m = 0; m < PINV_PER_T; ++m) { ah[m] = 0.0f; al[m] = 0.0f; }
+    for (int e = t; e < RR; e += nt) {
+      const int i = e / R, j = e % R;
+      float ah = 0.0f, al = 0.0f;
       for (int k = 0; k < R; ++k) {
-#pragma unroll
-        for (int m = 0; m < PINV_PER_T; ++m) {
-          if (ei[m] < 0) continue;
-          const float gh = Gh[ei[m] * R + k], gl = Gl[ei[m] * R + k];
-          const float xh = Xh[k * R + ej[m]], xl = Xl[k * R + ej[m]];
-          df_fma(ah[m], al[m], gh, xh);
-          al[m] = __fmaf_rn(gh, xl, __fmaf_rn(gl, xh, al[m]));
-        }
+        const float gh = Gh[i * R + k], gl = Gl[i * R + k], xh = Xh[k * R + j], xl = Xl[k * R + j];
+        df_fma(ah, al, gh, xh);
+        al = __fmaf_rn(gh, xl, __fmaf_rn(gl, xh, al));
       }
-#pragma unroll
-      for (int m = 0; m < PINV_PER_T; ++m) {
-        if (ei[m] < 0) continue;
-        const float ev = __fsub_rn(__fsub_rn(ei[m] == ej[m] ? 1.0f : 0.0f, ah[m]), al[m]);
-        W[t + m * nt] = ev;
-        emax = fmaxf(emax, fabsf(ev));
-      }
+      const float ev = __fsub_rn(__fsub_rn(i == j ? 1.0f : 0.0f, ah), al);
+      W[e] = ev;
+      emax = fmaxf(emax, fabsf(ev));
     }
     emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 16));
     emax = fmaxf(emax, __shfl_xor_sync(CPD_FULL, emax, 8));
@@ -342,11 +331,14 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     // X <- X + X W (the correction is small: float32 suffices)
     float corr[PINV_PER_T];
 #pragma unroll
-    for (int m = 0; m < PINV_PER_T; ++m) corr[m] = 0.0f;
-    for (int k = 0; k < R; ++k) {
-#pragma unroll
-      for (int m = 0; m < PINV_PER_T; ++m)
-        if (ei[m] >= 0) corr[m] = fmaf(Xh[ei[m] * R + k], W[k * R + ej[m]], corr[m]);
+    for (int m = 0; m < PINV_PER_T; ++m) {
+      const int e = t + m * nt;
+      float c = 0.0f;
+      if (e < RR) {
+        const int i = e / R, j = e % R;
+        for (int k = 0; k < R; ++k) c = fmaf(Xh[i * R + k], W[k * R + j], c);
+      }
+      corr[m] = c;
     }
     __syncthreads();
 #pragma unroll
