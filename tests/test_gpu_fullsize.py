@@ -76,3 +76,30 @@ def test_fullsize_sampled_mttkrp_and_solve(full):
     Un, sig_ref = oc.solve_and_renorm(Yg, oc.pinv_sym(G))
     assert rel_frob(cpd.cpd_get_factors(h, mode).double().cpu().numpy(), Un) <= 1e-5
     assert np.max(np.abs(sigma - sig_ref) / sig_ref) <= 1e-5
+
+
+def test_fullsize_sts_draws_match_oracle(full):
+    """STS-CP at the full size (leaf rows F = R = 32, a 12-level tree per
+    factor), in the launch configuration of `bench.py --method sts`: the
+    first 2,000 draws of a mode update equal the FP64 oracle's walk on the
+    same factors except within 1e-5 m(root) of a threshold (float32 masses),
+    with probabilities to 1e-5 relative."""
+    cpd, h_arls, idx, vals = full
+    dims, R = W["dims"], W["R"]
+    Jd = 2000
+    fs32 = [cpd.cpd_get_factors(h_arls, k) for k in range(3)]
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(), fs32, method="sts",
+                       rank=R, samples=W["J"], seed=W["sample_seed"])
+    fs = _factors(cpd, h)
+    grams = [oc.gram(U) for U in fs]
+    trees = [oc.sts_build(U, R) for U in fs]
+    for mode, sweep in ((1, 3),):
+        gi, gp = cpd.cpd_leverage_sample(h, mode, Jd, sweep)
+        oi, op, near = oc.sts_draw(trees, fs, grams, mode, Jd, W["sample_seed"], sweep, tie_tol=1e-5)
+        gi = gi.cpu().numpy()
+        mism = np.any(gi != oi, axis=0)
+        assert not np.any(mism & ~near), "STS draw differs away from a near-tie"
+        assert mism.mean() < 0.01
+        ok = ~mism
+        assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-5
+    h.close()
