@@ -209,6 +209,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_alloc(h, &h->uq_slot, (size_t)h->Jcap)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->chunk_seg, (size_t)cpd_ceil_div(std::max<int64_t>(nnz, 1), 32) + 1)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->uq_off, (size_t)h->Jcap + 1)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->uq_beg, (size_t)h->Jcap + 1)) != CPD_OK) return s;
   if ((s = cpd_alloc(h, &h->H, (size_t)h->Jcap * Rp)) != CPD_OK) return s;
 
   if (h->opt.method == CPD_ARLS_LEV) {

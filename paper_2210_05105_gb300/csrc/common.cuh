@@ -107,6 +107,7 @@ struct cpd_ctx {
   uint32_t* uq_slot = nullptr; // Jcap: dedup slot of each distinct column
   uint32_t* chunk_seg = nullptr; // ceil(nnz / 32): distinct column holding the first nonzero of each chunk
   uint32_t* uq_off = nullptr;  // Jcap: offset of each distinct column's nonzeros in the flat list
+  uint32_t* uq_beg = nullptr;  // Jcap: first entry of each distinct column in the mode layout
   float* H = nullptr;          // Jcap x Rp: KRP row of each distinct column
   uint32_t* counters = nullptr;// words 0-1: one 64-bit (distinct columns << 32 | nnz_sel)
   int* status = nullptr;       // latched device error (cpd_status)

@@ -30,6 +30,7 @@ struct MArgs {
   uint32_t* uq_slot;
   uint32_t* chunk_seg;
   uint32_t* uq_off;
+  uint32_t* uq_beg;
   float* H;
   uint32_t* counters;
   int* status;
@@ -115,7 +116,7 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
         const uint32_t sl = u;
         u = (uint32_t)(base >> 32) + (uint32_t)__popc(wm & ((1u << lane) - 1u));
         off = (uint32_t)(base & 0xffffffffull) + incl - mylen;
-        if (u < a.uq_cap) { a.uq_slot[u] = sl; a.uq_off[u] = off; }
+        if (u < a.uq_cap) { a.uq_slot[u] = sl; a.uq_off[u] = off; a.uq_beg[u] = beg; }
         else { cpd_set_status(a.status, CPD_ERR_CAPACITY); won = false; }
       }
     }
@@ -191,8 +192,10 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
     float scale = 0.0f;
     if (p < total) {
       useg = seg0 + loc;
+      // the entry's address does not wait for the dedup slot: the column's
+      // first entry was recorded by the probe
       const uint32_t slot = a.uq_slot[useg];
-      const uint32_t e = a.dd_tag[slot] + ((uint32_t)p - segoff);
+      const uint32_t e = a.uq_beg[useg] + ((uint32_t)p - segoff);
       const uint2 en = a.ent[e];
       row = en.x;
       scale = a.dd_w[slot] * __uint_as_float(en.y);
@@ -394,7 +397,7 @@ MArgs make_args(cpd_ctx* h, int mode) {
   a.mask = h->mode[mode].mask;
   a.ent = h->mode[mode].ent;
   a.dd_tag = h->dd_tag; a.dd_w = h->dd_w; a.dmask = h->dedup_mask;
-  a.uq_slot = h->uq_slot; a.chunk_seg = h->chunk_seg; a.uq_off = h->uq_off;
+  a.uq_slot = h->uq_slot; a.chunk_seg = h->chunk_seg; a.uq_off = h->uq_off; a.uq_beg = h->uq_beg;
   a.H = h->H; a.counters = h->counters; a.status = h->status;
   a.uq_cap = (uint32_t)h->Jcap;
   return a;
