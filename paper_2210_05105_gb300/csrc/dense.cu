@@ -15,6 +15,7 @@
 namespace {
 
 constexpr int TR = 64;          // rows per tile
+constexpr int TRP = TR + 4;     // padded column stride of the Gram tile (floats)
 constexpr int DTHREADS = 256;
 
 // ---- column sums of squares (float64 partials per block) ----------------
@@ -69,7 +70,8 @@ template <int MAXP>
 __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int fast) {
-  extern __shared__ float tile[];                      // TR x R float32
+  extern __shared__ float4 tile4[];
+  float* tile = reinterpret_cast<float*>(tile4);        // R columns x TRP float32
   __shared__ float inv[CPD_MAX_RANK];
   __shared__ unsigned char pa[8320], pb[8320];
   const int t = threadIdx.x;
@@ -97,6 +99,9 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
   const int64_t ntiles = cpd_ceil_div(I, TR);
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t r0 = tl * TR;
+    // tile column-major with a padded column stride TRP: column c of rows
+    // rr..rr+3 is one 16-byte read, and the eight lanes of a phase that read
+    // consecutive columns hit distinct banks
     for (int e = t; e < TR * Rp; e += DTHREADS) {
       int rr = e / Rp, c = e % Rp;
       int64_t i = r0 + rr;
@@ -104,9 +109,9 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
         float v = 0.0f;
         if (c < R) v = Uin[i * Rp + c] * inv[c];
         Uout[i * Rp + c] = v;
-        if (c < R) tile[rr * R + c] = v;
+        if (c < R) tile[c * TRP + rr] = v;
       } else if (c < R) {
-        tile[rr * R + c] = 0.0f;
+        tile[c * TRP + rr] = 0.0f;
       }
     }
     __syncthreads();
@@ -114,22 +119,25 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
     for (int m = 0; m < MAXP; ++m) {
       int p = t + m * DTHREADS;
       if (p < npairs) {
-        const int a = pa[p], b = pb[p];
+        const float4* ca = reinterpret_cast<const float4*>(tile + pa[p] * TRP);
+        const float4* cb = reinterpret_cast<const float4*>(tile + pb[p] * TRP);
         if (fast) {                      // float32 accumulation (precision option 1)
 #pragma unroll 4
-          for (int rr = 0; rr < TR; rr += 4) {
-            ah[m][0] = fmaf(tile[rr * R + a], tile[rr * R + b], ah[m][0]);
-            ah[m][1] = fmaf(tile[(rr + 1) * R + a], tile[(rr + 1) * R + b], ah[m][1]);
-            ah[m][2] = fmaf(tile[(rr + 2) * R + a], tile[(rr + 2) * R + b], ah[m][2]);
-            ah[m][3] = fmaf(tile[(rr + 3) * R + a], tile[(rr + 3) * R + b], ah[m][3]);
+          for (int q = 0; q < TR / 4; ++q) {
+            const float4 x = ca[q], y = cb[q];
+            ah[m][0] = fmaf(x.x, y.x, ah[m][0]);
+            ah[m][1] = fmaf(x.y, y.y, ah[m][1]);
+            ah[m][2] = fmaf(x.z, y.z, ah[m][2]);
+            ah[m][3] = fmaf(x.w, y.w, ah[m][3]);
           }
         } else {
 #pragma unroll 4
-          for (int rr = 0; rr < TR; rr += 4) {
-            df_fma(ah[m][0], al[m][0], tile[rr * R + a], tile[rr * R + b]);
-            df_fma(ah[m][1], al[m][1], tile[(rr + 1) * R + a], tile[(rr + 1) * R + b]);
-            df_fma(ah[m][2], al[m][2], tile[(rr + 2) * R + a], tile[(rr + 2) * R + b]);
-            df_fma(ah[m][3], al[m][3], tile[(rr + 3) * R + a], tile[(rr + 3) * R + b]);
+          for (int q = 0; q < TR / 4; ++q) {
+            const float4 x = ca[q], y = cb[q];
+            df_fma(ah[m][0], al[m][0], x.x, y.x);
+            df_fma(ah[m][1], al[m][1], x.y, y.y);
+            df_fma(ah[m][2], al[m][2], x.z, y.z);
+            df_fma(ah[m][3], al[m][3], x.w, y.w);
           }
         }
       }
@@ -683,7 +691,7 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
     CPD_LAUNCH(h, "gram_reduce");
     return CPD_OK;
   }
-  size_t shm = (size_t)TR * R * sizeof(float);
+  size_t shm = (size_t)TRP * R * sizeof(float);
   const int npairs = R * (R + 1) / 2;
   // Gram entries per thread: ceil(npairs / 256) rounded up to 1, 3, 9 or 33
   if (npairs <= DTHREADS)
@@ -812,7 +820,7 @@ cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out) {
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in.
 cpd_status cpd_dense_init(cpd_ctx* h) {
   const int R = h->R;
-  size_t s1 = (size_t)TR * R * sizeof(float);
+  size_t s1 = (size_t)TRP * R * sizeof(float);
   size_t s2 = pinv_smem(R);
   size_t s3 = (size_t)(2 * R * solve_rb(R)) * sizeof(float);
   const std::pair<const void*, size_t> attrs[] = {
