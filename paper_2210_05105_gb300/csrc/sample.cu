@@ -52,23 +52,46 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
   if (i < I) {
     float lh = 0.0f, ll = 0.0f;
     int p = 0;
-    if (fast) {                          // float32 (precision option 1)
+    if (fast) {                          // float32 (precision option 1), two chains
+      float l2 = 0.0f;
       for (int a = 0; a < R; ++a) {
         const float ua = us[a * (LEV_THREADS + 1) + t];
-        for (int b = a; b < R; ++b, ++p) lh = fmaf(ua * us[b * (LEV_THREADS + 1) + t], Xs[p].x, lh);
+        int b = a;
+        for (; b + 1 < R; b += 2, p += 2) {
+          lh = fmaf(ua * us[b * (LEV_THREADS + 1) + t], Xs[p].x, lh);
+          l2 = fmaf(ua * us[(b + 1) * (LEV_THREADS + 1) + t], Xs[p + 1].x, l2);
+        }
+        if (b < R) { lh = fmaf(ua * us[b * (LEV_THREADS + 1) + t], Xs[p].x, lh); ++p; }
       }
+      lh += l2;
     } else {
+      // two independent df64 chains (even and odd b) for instruction-level
+      // parallelism; merged at the end
+      float lh2 = 0.0f, ll2 = 0.0f;
       for (int a = 0; a < R; ++a) {
         const float ua = us[a * (LEV_THREADS + 1) + t];
-        for (int b = a; b < R; ++b, ++p) {
+        int b = a;
+        for (; b + 1 < R; b += 2, p += 2) {
+          const float ub0 = us[b * (LEV_THREADS + 1) + t], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t];
+          const float2 x0 = Xs[p], x1 = Xs[p + 1];
+          const float ph0 = __fmul_rn(ua, ub0), ph1 = __fmul_rn(ua, ub1);
+          const float pl0 = __fmaf_rn(ua, ub0, -ph0), pl1 = __fmaf_rn(ua, ub1, -ph1);
+          df_fma(lh, ll, ph0, x0.x);
+          df_fma(lh2, ll2, ph1, x1.x);
+          ll = __fmaf_rn(pl0, x0.x, __fmaf_rn(ph0, x0.y, ll));
+          ll2 = __fmaf_rn(pl1, x1.x, __fmaf_rn(ph1, x1.y, ll2));
+        }
+        if (b < R) {
           const float ub = us[b * (LEV_THREADS + 1) + t];
           const float2 x = Xs[p];
           const float ph = __fmul_rn(ua, ub);
           const float pl = __fmaf_rn(ua, ub, -ph);
           df_fma(lh, ll, ph, x.x);
           ll = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll));
+          ++p;
         }
       }
+      df_merge(lh, ll, lh2, ll2);
     }
     l = df_value(lh, ll);
     ell[i] = l;
