@@ -228,10 +228,11 @@ __device__ __forceinline__ dd dd_sub(dd a, dd b) {
   df_two_sum(a.h, -b.h, s, e);
   return dd_norm(s, __fadd_rn(e, __fsub_rn(a.l, b.l)));
 }
-__device__ __forceinline__ dd dd_neg(dd a) { return {-a.h, -a.l}; }
-// 1 / a: float32 reciprocal r, then r + r (1 - a r) in df64 (~2^-46 relative)
+// 1 / a: approximate float32 reciprocal r, then r + r (1 - a r) in df64
+// (~2^-46 relative: the refinement squares the start's error)
 __device__ __forceinline__ dd dd_recip(dd a) {
-  const float r = 1.0f / a.h;
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(a.h));
   const dd res = dd_sub(dd{1.0f, 0.0f}, dd_mul(a, dd{r, 0.0f}));
   const dd c = dd_mul(dd{r, 0.0f}, res);
   float s, e;
@@ -301,9 +302,14 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
       const int i = ei[m], j = ej[m];
       if (i < 0) continue;
       const dd rj{rowk[b][j].x, rowk[b][j].y}, ci{colk[b][i].x, colk[b][i].y};
-      if (i == k) w[m] = (j == k) ? inv : dd_mul(rj, inv);
-      else if (j == k) w[m] = dd_neg(dd_mul(ci, inv));
-      else w[m] = dd_sub(w[m], dd_mul(ci, dd_mul(rj, inv)));
+      // branch-free step: the pivot column is treated as the identity column
+      // (r_k := 1, w := 0 there), so every entry runs the same instructions
+      const bool jk = (j == k);
+      const dd r1{jk ? 1.0f : rj.h, jk ? 0.0f : rj.l};
+      const dd wb{jk ? 0.0f : w[m].h, jk ? 0.0f : w[m].l};
+      const dd sv = dd_mul(r1, inv);
+      const dd gv = dd_sub(wb, dd_mul(ci, sv));
+      w[m] = (i == k) ? sv : gv;
     }
   }
 #pragma unroll
