@@ -371,7 +371,13 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
   if (!ok) return false;
   for (int e = t; e < RR; e += nt) {
     const int i = e / R, j = e % R;
-    jb.out_pinv[e] = 0.5 * (df_value(Xh[e], Xl[e]) + df_value(Xh[j * R + i], Xl[j * R + i]));
+    const double p = 0.5 * (df_value(Xh[e], Xl[e]) + df_value(Xh[j * R + i], Xl[j * R + i]));
+    jb.out_pinv[e] = p;
+    if (jb.out_split) {               // the solve's float32 hi + lo copy
+      const float hi = (float)p;
+      jb.out_split[e] = hi;
+      jb.out_split[RR + e] = (float)(p - (double)hi);
+    }
   }
   return true;
 }
@@ -382,7 +388,9 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
 // Jacobi eigendecomposition with eigenvalues <= R 2^-52 lambda_max dropped.
 // One block; each elimination step copies row and column k aside, then every
 // thread updates its entries (two barriers per step, no serial thread).
-__device__ __forceinline__ void pinv_body(const PinvJob& jb, int R, int fast) {
+// Returns whether the float32 split of the result was written too (the fast
+// path writes it with the result).
+__device__ __forceinline__ bool pinv_body(const PinvJob& jb, int R, int fast) {
   extern __shared__ double A[];                     // R x R
   __shared__ double red[40];
   __shared__ int sp[64], sq[64];
@@ -390,7 +398,7 @@ __device__ __forceinline__ void pinv_body(const PinvJob& jb, int R, int fast) {
   __shared__ double rowk[CPD_MAX_RANK], colk[CPD_MAX_RANK];
   const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
-  if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6)) return;
+  if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6)) return true;
   for (int e = t; e < RR; e += nt) {
     double v = 1.0;
     for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
@@ -423,7 +431,7 @@ __device__ __forceinline__ void pinv_body(const PinvJob& jb, int R, int fast) {
       const int i = e / R, j = e % R;
       jb.out_pinv[e] = 0.5 * (A[e] + A[j * R + i]);
     }
-    return;
+    return false;
   }
   // -- Jacobi fallback: reload A, V = I
   __syncthreads();
@@ -507,14 +515,16 @@ __device__ __forceinline__ void pinv_body(const PinvJob& jb, int R, int fast) {
     }
     jb.out_pinv[e] = s;
   }
+  return false;
 }
 
 // Every path of pinv_body leaves the block together, so the float32 split of
-// the result (the solve's operand) can follow one barrier later.
+// the result (the solve's operand), when the fast path did not write it, can
+// follow one barrier later.
 __global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R, int fast) {
   const PinvJob& jb = jobs.job[blockIdx.x];
-  pinv_body(jb, R, fast);
-  if (jb.out_split) {
+  const bool split_done = pinv_body(jb, R, fast);
+  if (jb.out_split && !split_done) {
     __syncthreads();
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
       const double p = jb.out_pinv[e];
