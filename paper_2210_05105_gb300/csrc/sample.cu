@@ -147,27 +147,56 @@ struct DrawArgs {
 // Algorithm 3 with one processor: per factor k != n, i_k = smallest i with
 // cdf_k[i] > u * C_k (past the end: the row where the running sum reaches C_k).
 // A factor with C_k = 0 (all scores zero) draws row 0 with probability 0.
+template <int NM>   // NM >= N
 __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long* __restrict__ d_sweep,
                                  unsigned long long h_sweep, int32_t* __restrict__ out_idx,
                                  double* __restrict__ out_p, double* __restrict__ out_w) {
   const unsigned long long s = d_sweep ? *d_sweep : h_sweep;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
-    double p = 1.0;
-    for (int k = 0; k < a.N; ++k) {
+    // the factors' binary searches advance together (their loads overlap)
+    int64_t lo[NM], hi[NM];
+    long long tb[NM];
+    double t[NM], C[NM];
+    bool zero = false;
+    int steps = 0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      lo[k] = 0; hi[k] = 0; tb[k] = 0; t[k] = 0.0; C[k] = 0.0;
+      if (k >= a.N) continue;
       if (k == a.n) { out_idx[(int64_t)k * J + j] = -1; continue; }
-      const double* cdf = a.cdf[k];
       const int64_t I = a.dims[k];
-      const double C = cdf[I - 1];
-      if (!(C > 0.0) || !isfinite(C)) {     // all scores zero: no distribution, weight 0
-        out_idx[(int64_t)k * J + j] = 0;
-        p = 0.0;
+      C[k] = a.cdf[k][I - 1];
+      if (!(C[k] > 0.0) || !isfinite(C[k])) {     // all scores zero: no distribution, weight 0
+        zero = true;
         continue;
       }
-      const double t = cpd_uniform(a.seed, CPD_STREAM_ARLS, (unsigned long long)j, (unsigned long long)k,
-                                   (unsigned long long)a.n, s) * C;
-      const int64_t lo = cpd_inverse_cdf(cdf, I, t);
-      out_idx[(int64_t)k * J + j] = (int32_t)lo;
-      p *= a.ell[k][lo] / C;
+      t[k] = cpd_uniform(a.seed, CPD_STREAM_ARLS, (unsigned long long)j, (unsigned long long)k,
+                         (unsigned long long)a.n, s) * C[k];
+      tb[k] = __double_as_longlong(t[k]);       // non-negative: bit order = value order
+      hi[k] = I;
+      int d = 0;
+      while ((int64_t(1) << d) <= I) ++d;
+      steps = d > steps ? d : steps;
+    }
+    for (int it = 0; it < steps; ++it) {
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        if (lo[k] < hi[k]) {
+          const int64_t mid = (lo[k] + hi[k]) >> 1;
+          if (reinterpret_cast<const long long*>(a.cdf[k])[mid] > tb[k]) hi[k] = mid; else lo[k] = mid + 1;
+        }
+      }
+    }
+    double p = zero ? 0.0 : 1.0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      if (k >= a.N || k == a.n) continue;
+      const int64_t I = a.dims[k];
+      if (!(C[k] > 0.0) || !isfinite(C[k])) { out_idx[(int64_t)k * J + j] = 0; continue; }
+      int64_t i = lo[k];
+      if (i >= I) i = cpd_inverse_cdf(a.cdf[k], I, t[k]);   // t rounded up to C: rare
+      out_idx[(int64_t)k * J + j] = (int32_t)i;
+      if (!zero) p *= a.ell[k][i] / C[k];
     }
     if (out_p) out_p[j] = p;
     if (out_w) out_w[j] = cpd_weight(J, p);
@@ -235,7 +264,10 @@ cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d
   if (J <= 0) return CPD_OK;
   PhaseTimer pt(h, CPD_PHASE_DRAW);
   int grid = (int)std::min<int64_t>(cpd_ceil_div(J, 256), (int64_t)h->num_sms * 8);
-  arls_draw_kernel<<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
+  if (h->N <= 4)
+    arls_draw_kernel<4><<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
+  else
+    arls_draw_kernel<CPD_MAX_MODES><<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
   CPD_LAUNCH(h, "arls_draw");
   return CPD_OK;
 }
