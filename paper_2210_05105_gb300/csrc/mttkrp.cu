@@ -150,11 +150,45 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
   }
 }
 
+// One step of a lane group: selected position jj of the chunk (row code r,
+// weight sj, distinct column uj, all shuffled from lane jj) adds sj * h_uj
+// into its output row.  The lane group's KRP row hv stays in registers while
+// the drawn column does not change.
+__device__ __forceinline__ void spmm_step(const MArgs& a, int Rp, int C, int q, int Hs, float* __restrict__ hot_acc,
+                                          float* __restrict__ Y, uint32_t r, float sj, uint32_t uj, uint32_t& cu,
+                                          float4& hv) {
+  if (uj != cu) {
+    hv = reinterpret_cast<const float4*>(a.H)[(int64_t)uj * C + q];
+    cu = uj;
+  }
+  if (r & CPD_HOT_BIT) {
+    const uint32_t slot = r & ~CPD_HOT_BIT;
+    if ((int)slot < Hs) {
+      float* acc = hot_acc + (size_t)slot * (Rp + 1) + 4 * q;
+      atomicAdd(acc + 0, sj * hv.x);
+      atomicAdd(acc + 1, sj * hv.y);
+      atomicAdd(acc + 2, sj * hv.z);
+      atomicAdd(acc + 3, sj * hv.w);
+      reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * (Rp + 1))[slot] = 1u;
+      return;
+    }
+    r = (uint32_t)a.hot_rows[slot];
+  }
+  float* yp = Y + (int64_t)r * Rp + 4 * q;
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj * hv.x), "f"(sj * hv.y),
+               "f"(sj * hv.z), "f"(sj * hv.w)
+               : "memory");
+}
+
+// RPT: the row stride Rp as a compile-time constant (lane-group shape and
+// address arithmetic fold), or 0 for a.Rp at run time.
+template <int RPT>
 __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
   // hot rows: one float row (stride Rp + 1, so rows start in different banks)
   // per slot, and a touched flag per slot; flushed to Y once per block
   extern __shared__ float hot_acc[];
-  const int S = a.Rp + 1;
+  const int Rp = RPT ? RPT : a.Rp;
+  const int S = Rp + 1;
   const int Hs = a.n_hot;
   unsigned int* touched = reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * S);
   for (int i = threadIdx.x; i < Hs * S; i += blockDim.x) hot_acc[i] = 0.0f;
@@ -168,7 +202,7 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
   const uint32_t total = (uint32_t)(pk & 0xffffffffull);
   if (out_nnz_sel && blockIdx.x == 0 && threadIdx.x == 0) *out_nnz_sel = (int64_t)total;
   const int64_t nchunks = ((int64_t)total + 31) / 32;
-  const int C = a.Rp / 4;                 // float4 chunks per row
+  const int C = Rp / 4;                   // float4 chunks per row
   const int E = C >= 32 ? 1 : 32 / C;     // nonzeros per warp instruction
   const int sub = C >= 32 ? 0 : lane / C; // which of the E nonzeros this lane serves
   const int q = C >= 32 ? lane : lane % C;
@@ -206,37 +240,30 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
     // selected nonzeros at once.  Consecutive positions of a lane group
     // mostly belong to the same drawn column, so its KRP row is kept in
     // registers and loaded again only when the column changes.
-    const float4* H4 = reinterpret_cast<const float4*>(a.H);
     uint32_t cu = 0xffffffffu;
     float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int j0 = 0; j0 < cnt; j0 += E) {
-      const int jj = j0 + sub;
-      const int src = jj < 32 ? jj : 31;
-      uint32_t r = __shfl_sync(CPD_FULL, row, src);
-      const float sj = __shfl_sync(CPD_FULL, scale, src);
-      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
-      if (!(sub < E && jj < cnt)) continue;
-      if (uj != cu) {
-        hv = H4[(int64_t)uj * C + q];
-        cu = uj;
+    if (RPT && E * C == 32 && cnt == 32) {
+      // a full chunk and a lane-group shape that fills the warp: every step
+      // is valid (four steps unrolled at Rp >= 32, two at Rp = 16: more would
+      // spill at 32 registers)
+#pragma unroll (RPT >= 32 ? 4 : 2)
+      for (int j0 = 0; j0 < 32; j0 += E) {
+        const int jj = j0 + sub;
+        const uint32_t r = __shfl_sync(CPD_FULL, row, jj);
+        const float sj = __shfl_sync(CPD_FULL, scale, jj);
+        const uint32_t uj = __shfl_sync(CPD_FULL, useg, jj);
+        spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
       }
-      if (r & CPD_HOT_BIT) {
-        const uint32_t slot = r & ~CPD_HOT_BIT;
-        if ((int)slot < Hs) {
-          float* acc = hot_acc + (size_t)slot * S + 4 * q;
-          atomicAdd(acc + 0, sj * hv.x);
-          atomicAdd(acc + 1, sj * hv.y);
-          atomicAdd(acc + 2, sj * hv.z);
-          atomicAdd(acc + 3, sj * hv.w);
-          touched[slot] = 1u;
-          continue;
-        }
-        r = (uint32_t)a.hot_rows[slot];
+    } else {
+      for (int j0 = 0; j0 < cnt; j0 += E) {
+        const int jj = j0 + sub;
+        const int src = jj < 32 ? jj : 31;
+        const uint32_t r = __shfl_sync(CPD_FULL, row, src);
+        const float sj = __shfl_sync(CPD_FULL, scale, src);
+        const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
+        if (!(sub < E && jj < cnt)) continue;
+        spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
       }
-      float* yp = Y + (int64_t)r * a.Rp + 4 * q;
-      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj * hv.x), "f"(sj * hv.y),
-                   "f"(sj * hv.z), "f"(sj * hv.w)
-                   : "memory");
     }
   }
   // flush the block's hot rows that it touched
@@ -245,7 +272,7 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
     const int slot = i / C, qq = i - slot * C;
     if (!touched[slot]) continue;
     const float* acc = hot_acc + (size_t)slot * S + 4 * qq;
-    float* yp = Y + (int64_t)a.hot_rows[slot] * a.Rp + 4 * qq;
+    float* yp = Y + (int64_t)a.hot_rows[slot] * Rp + 4 * qq;
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[1]), "f"(acc[2]),
                  "f"(acc[3])
                  : "memory");
@@ -376,8 +403,11 @@ int cpd_spmm_hot_slots(int Rp, int bps) {
 }
 cpd_status cpd_spmm_init(cpd_ctx* h) {
   const size_t shm = (size_t)cpd_spmm_hot_slots(h->Rp, 1) * ((size_t)(h->Rp + 1) * 4 + 4);
-  const cpd_status s = cpd_smem_attr(h, (const void*)spmm_kernel, shm);
-  if (s != CPD_OK) return s;
+  for (const void* f : {(const void*)spmm_kernel<0>, (const void*)spmm_kernel<16>, (const void*)spmm_kernel<32>,
+                        (const void*)spmm_kernel<64>, (const void*)spmm_kernel<128>}) {
+    const cpd_status s = cpd_smem_attr(h, f, shm);
+    if (s != CPD_OK) return s;
+  }
   const cpd_status s4 = cpd_smem_attr(h, (const void*)exact_kernel<4>, shm);
   return s4 != CPD_OK ? s4 : cpd_smem_attr(h, (const void*)exact_kernel<CPD_MAX_MODES>, shm);
 }
@@ -441,7 +471,14 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
     a.n_hot = std::min(h->mode[mode].n_hot, cpd_spmm_hot_slots(h->Rp, bps));
     a.hot_rows = h->mode[mode].hot_rows;
     const size_t shm = (size_t)a.n_hot * ((size_t)(h->Rp + 1) * 4 + 4);
-    spmm_kernel<<<h->num_sms * bps, cpd_spmm_threads(bps), shm, st>>>(a, Y, out_nnz_sel);
+    const dim3 grid(h->num_sms * bps), block(cpd_spmm_threads(bps));
+    switch (h->Rp) {
+      case 16: spmm_kernel<16><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
+      case 32: spmm_kernel<32><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
+      case 64: spmm_kernel<64><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
+      case 128: spmm_kernel<128><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
+      default: spmm_kernel<0><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
+    }
     CPD_LAUNCH(h, "spmm");
   }
   if (h->opt.sketched_gram) return cpd_sketch_gram(h, mode, idx, w, J);
