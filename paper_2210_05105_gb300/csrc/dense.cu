@@ -619,6 +619,97 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
   }
 }
 
+// ---- solve for R <= 32: one output column per lane ------------------------
+// Lane c of every warp owns output column c and holds column c of P_hi and
+// P_lo in registers.  The block stages SOLVE_TR rows of Y in shared memory
+// (the next tile is loaded into registers while the current one is used);
+// warp w takes rows w, w + 8, ... of the tile, two at a time, reading each
+// row as 16-byte broadcasts.  Every output sums its terms in the same order
+// as solve_kernel: o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
+constexpr int SOLVE_TR = 64;
+__global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
+    const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R, int Rp,
+    double* __restrict__ colpart) {
+  constexpr int RB = 32;
+  __shared__ float4 ys4[SOLVE_TR * RB / 4];       // tile row r at r * RB / 4; columns >= Rp stay zero
+  __shared__ float wsq[DTHREADS / 32][32];
+  const int t = threadIdx.x, c = t & 31, wid = t >> 5;
+  float ph[RB], pl[RB];
+#pragma unroll
+  for (int a = 0; a < RB; ++a) {
+    const bool in = a < R && c < R;
+    ph[a] = in ? P2[a * R + c] : 0.0f;
+    pl[a] = in ? P2[R * R + a * R + c] : 0.0f;
+  }
+  const int C4 = Rp / 4;                          // float4 per row of Y (Rp <= 32)
+  const int nv = SOLVE_TR * C4;                   // float4 per tile (<= 512 = 2 per thread)
+  for (int e = t; e < SOLVE_TR * RB / 4; e += DTHREADS) ys4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4* Y4 = reinterpret_cast<const float4*>(Y);
+  float4 pre[2];
+  auto load_tile = [&](int64_t r0) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = t + k * DTHREADS;
+      pre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < nv) {
+        const int row = e / C4, c4 = e - row * C4;
+        if (r0 + row < I) pre[k] = Y4[(r0 + row) * C4 + c4];
+      }
+    }
+  };
+  float csq = 0.0f;
+  int64_t r0 = (int64_t)blockIdx.x * SOLVE_TR;
+  if (r0 < I) load_tile(r0);
+  for (; r0 < I; r0 += (int64_t)gridDim.x * SOLVE_TR) {
+    __syncthreads();                              // the previous tile has been used
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = t + k * DTHREADS;
+      if (e < nv) {
+        const int row = e / C4, c4 = e - row * C4;
+        ys4[row * (RB / 4) + c4] = pre[k];
+      }
+    }
+    __syncthreads();
+    const int64_t rn = r0 + (int64_t)gridDim.x * SOLVE_TR;
+    if (rn < I) load_tile(rn);
+    for (int rr = wid; rr < SOLVE_TR; rr += 16) {   // rows rr and rr + 8 of the tile
+      const float4* y0 = ys4 + rr * (RB / 4);
+      const float4* y1 = ys4 + (rr + 8) * (RB / 4);
+      float o0 = 0.0f, o1 = 0.0f;
+#pragma unroll
+      for (int v = 0; v < RB / 4; ++v) {
+        const float4 a0 = y0[v], a1 = y1[v];
+        o0 = fmaf(a0.x, ph[4 * v], fmaf(a0.x, pl[4 * v], o0));
+        o1 = fmaf(a1.x, ph[4 * v], fmaf(a1.x, pl[4 * v], o1));
+        o0 = fmaf(a0.y, ph[4 * v + 1], fmaf(a0.y, pl[4 * v + 1], o0));
+        o1 = fmaf(a1.y, ph[4 * v + 1], fmaf(a1.y, pl[4 * v + 1], o1));
+        o0 = fmaf(a0.z, ph[4 * v + 2], fmaf(a0.z, pl[4 * v + 2], o0));
+        o1 = fmaf(a1.z, ph[4 * v + 2], fmaf(a1.z, pl[4 * v + 2], o1));
+        o0 = fmaf(a0.w, ph[4 * v + 3], fmaf(a0.w, pl[4 * v + 3], o0));
+        o1 = fmaf(a1.w, ph[4 * v + 3], fmaf(a1.w, pl[4 * v + 3], o1));
+      }
+      const int64_t i0 = r0 + rr, i1 = r0 + rr + 8;
+      if (i0 < I) {
+        if (c < Rp) Uw[i0 * Rp + c] = o0;
+        csq = fmaf(o0, o0, csq);
+      }
+      if (i1 < I) {
+        if (c < Rp) Uw[i1 * Rp + c] = o1;
+        csq = fmaf(o1, o1, csq);
+      }
+    }
+  }
+  // (float32 suffices: a lane holds a few rows; float64 only per block)
+  wsq[wid][c] = csq;
+  __syncthreads();
+  for (int cc = t; cc < R; cc += DTHREADS) {
+    double s = 0.0;
+    for (int w = 0; w < DTHREADS / 32; ++w) s += (double)wsq[w][cc];
+    colpart[(int64_t)blockIdx.x * R + cc] = s;
+  }
+}
+
 static int solve_rb(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
 
 // ---- fit ------------------------------------------------------------------
@@ -796,16 +887,19 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     PhaseTimer pt(h, CPD_PHASE_SOLVE);
     const int rb = solve_rb(R);
     size_t shm = (size_t)(2 * R * rb) * sizeof(float);
-    if (rb == 16)
+    int nblk = h->gram_blocks;                  // column partials summed by sigma_kernel
+    if (rb == 32) {
+      // two resident blocks per SM (118 registers a thread)
+      nblk = (int)std::min<int64_t>(std::min(nblk, h->num_sms * 2), std::max<int64_t>(cpd_ceil_div(I, SOLVE_TR), 1));
+      solve_lane_kernel<<<nblk, DTHREADS, 0, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
+    } else if (rb == 16)
       solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
-    else if (rb == 32)
-      solve_kernel<32><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else if (rb == 64)
       solve_kernel<64><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else
       solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     CPD_LAUNCH(h, "solve");
-    sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, h->gram_blocks, R, h->sigma);
+    sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, nblk, R, h->sigma);
     CPD_LAUNCH(h, "sigma");
   }
   if (out_sigma && out_sigma != h->sigma)

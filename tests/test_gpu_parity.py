@@ -256,13 +256,24 @@ def test_rank_deficient_gram_uses_pseudo_inverse(cpd):
 
 
 def test_odd_rank_and_ragged_tiles(cpd):
-    """R = 25 (not a multiple of 4) and modes that are not tile multiples."""
+    """R = 25 (not a multiple of 4: padded row stride 28) and modes that are
+    not tile multiples (the solve's 64-row tiles end ragged at 97 and 1031
+    rows)."""
     dims = (333, 97, 1031)
     idx, vals, init = make_case(dims, 30000, 25, seed=90)
     h = create(cpd, dims, idx, vals, init, "arls", 25, 3000, seed=9)
     fs = gpu_factors(cpd, h)
     for k in range(3):
         assert rel_frob(cpd.cpd_get_gram(h, k).cpu().numpy(), oc.gram(fs[k])) < 1e-13
+    rng = np.random.default_rng(25)
+    for mode in (1, 2):
+        Ys = rng.standard_normal((dims[mode], 25)).astype(np.float32)
+        sigma = cpd.cpd_gram_solve(h, mode, torch.from_numpy(Ys)).cpu().numpy()
+        G = oc.hadamard_of_grams([oc.gram(U) for U in fs], mode)
+        U_ref, s_ref = oc.solve_and_renorm(Ys.astype(np.float64), oc.pinv_sym(G))
+        assert rel_frob(sigma, s_ref) < 1e-5
+        assert rel_frob(cpd.cpd_get_factors(h, mode).double().cpu().numpy(), U_ref) < 1e-5
+        fs[mode] = cpd.cpd_get_factors(h, mode).double().cpu().numpy()
     oi, op = _oracle_samples(fs, 2, 3000, 9, 0)
     gi, gp = cpd.cpd_leverage_sample(h, 2, 3000, 0)
     w = 1.0 / (3000 * op)
