@@ -142,15 +142,35 @@ struct DrawArgs {
   int64_t dims[CPD_MAX_MODES];
   int N, n;
   unsigned long long seed;
+  int64_t sstride;            // every sstride-th running sum is staged in shared memory
+  int soff[CPD_MAX_MODES];    // factor k's samples: soff[k] .. soff[k] + scnt[k] - 1
+  int scnt[CPD_MAX_MODES];    // ceil(I_k / sstride) (0 for the mode being updated)
 };
+constexpr int DRAW_THREADS = 512;
+constexpr size_t DRAW_SMEM = 46 * 1024;   // staged samples of the running sums (no opt-in needed)
 
 // Algorithm 3 with one processor: per factor k != n, i_k = smallest i with
 // cdf_k[i] > u * C_k (past the end: the row where the running sum reaches C_k).
 // A factor with C_k = 0 (all scores zero) draws row 0 with probability 0.
+// The block first stages every sstride-th running sum of each factor in
+// shared memory; a draw's binary search runs there first (m = first staged
+// sample above t), which brackets i_k to the sstride rows after sample m - 1,
+// and only that bracket is searched in global memory.  For non-decreasing
+// running sums the result is the full search's.
 template <int NM>   // NM >= N
-__global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long* __restrict__ d_sweep,
-                                 unsigned long long h_sweep, int32_t* __restrict__ out_idx,
-                                 double* __restrict__ out_p, double* __restrict__ out_w) {
+__global__ void __launch_bounds__(DRAW_THREADS) arls_draw_kernel(DrawArgs a, int64_t J,
+                                                                 const unsigned long long* __restrict__ d_sweep,
+                                                                 unsigned long long h_sweep,
+                                                                 int32_t* __restrict__ out_idx,
+                                                                 double* __restrict__ out_p, double* __restrict__ out_w) {
+  extern __shared__ long long samp[];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) {
+    if (k >= a.N || a.scnt[k] == 0) continue;
+    const long long* cb = reinterpret_cast<const long long*>(a.cdf[k]);
+    for (int m = threadIdx.x; m < a.scnt[k]; m += blockDim.x) samp[a.soff[k] + m] = cb[(int64_t)m * a.sstride];
+  }
+  __syncthreads();
   const unsigned long long s = d_sweep ? *d_sweep : h_sweep;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
     // the factors' binary searches advance together (their loads overlap)
@@ -173,9 +193,19 @@ __global__ void arls_draw_kernel(DrawArgs a, int64_t J, const unsigned long long
       t[k] = cpd_uniform(a.seed, CPD_STREAM_ARLS, (unsigned long long)j, (unsigned long long)k,
                          (unsigned long long)a.n, s) * C[k];
       tb[k] = __double_as_longlong(t[k]);       // non-negative: bit order = value order
-      hi[k] = I;
+      // staged samples: m = first sample above t, so rows <= (m - 1) sstride
+      // have running sums <= t and row m sstride (if it exists) one above t
+      const long long* sk = samp + a.soff[k];
+      int ml = 0, mh = a.scnt[k];
+      while (ml < mh) {
+        const int mid = (ml + mh) >> 1;
+        if (sk[mid] > tb[k]) mh = mid; else ml = mid + 1;
+      }
+      lo[k] = ml == 0 ? 0 : (int64_t)(ml - 1) * a.sstride + 1;
+      hi[k] = ml < a.scnt[k] ? (int64_t)ml * a.sstride : I;
+      if (lo[k] > hi[k]) lo[k] = hi[k];
       int d = 0;
-      while ((int64_t(1) << d) <= I) ++d;
+      while ((int64_t(1) << d) <= hi[k] - lo[k]) ++d;
       steps = d > steps ? d : steps;
     }
     for (int it = 0; it < steps; ++it) {
@@ -263,11 +293,30 @@ cpd_status cpd_draw(cpd_ctx* h, int mode, int64_t J, const unsigned long long* d
   a.N = h->N; a.n = mode; a.seed = h->opt.seed;
   if (J <= 0) return CPD_OK;
   PhaseTimer pt(h, CPD_PHASE_DRAW);
-  int grid = (int)std::min<int64_t>(cpd_ceil_div(J, 256), (int64_t)h->num_sms * 8);
+  // the smallest power-of-two stride whose samples of all factors fit
+  int64_t st = 1;
+  for (;;) {
+    int64_t tot = 0;
+    for (int k = 0; k < h->N; ++k)
+      if (k != mode) tot += cpd_ceil_div(h->dims[k], st);
+    if (tot * (int64_t)sizeof(long long) <= (int64_t)DRAW_SMEM) break;
+    st *= 2;
+  }
+  a.sstride = st;
+  int off = 0;
+  for (int k = 0; k < h->N; ++k) {
+    a.soff[k] = off;
+    a.scnt[k] = k == mode ? 0 : (int)cpd_ceil_div(h->dims[k], st);
+    off += a.scnt[k];
+  }
+  const size_t shm = (size_t)off * sizeof(long long);
+  // at most two blocks per SM: the samples are staged once per block
+  int grid = (int)std::min<int64_t>(cpd_ceil_div(J, DRAW_THREADS), (int64_t)h->num_sms * 2);
   if (h->N <= 4)
-    arls_draw_kernel<4><<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
+    arls_draw_kernel<4><<<grid, DRAW_THREADS, shm, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
   else
-    arls_draw_kernel<CPD_MAX_MODES><<<grid, 256, 0, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p, out_w);
+    arls_draw_kernel<CPD_MAX_MODES><<<grid, DRAW_THREADS, shm, h->stream>>>(a, J, d_sweep, sweep, out_idx, out_p,
+                                                                            out_w);
   CPD_LAUNCH(h, "arls_draw");
   return CPD_OK;
 }

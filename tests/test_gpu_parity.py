@@ -72,6 +72,28 @@ def test_arls_draws_match_oracle_exactly(cpd, mode, sweep):
     h.close()
 
 
+@pytest.mark.parametrize("dims,mode", [((6007, 5003, 4001), 0), ((6007, 5003, 4001), 2),
+                                       ((3001, 2003, 1009, 17, 11), 4)])
+def test_arls_draws_with_staged_running_sums(cpd, dims, mode):
+    """Factors long enough that the draw kernel stages only every 2nd or
+    4th running sum in shared memory (ragged last stride; a 5-mode tensor
+    takes the 8-mode kernel): every draw equals the oracle's inverse-CDF draw
+    (ties excepted), across 40 blocks of draws."""
+    R, J = 8, 20000
+    idx, vals, init = make_case(dims, 30000, R, seed=41)
+    h = create(cpd, dims, idx, vals, init, "arls", R, J, seed=77)
+    fs = gpu_factors(cpd, h)
+    samplers = [oc.arls_build(U) for U in fs]
+    gi, gp = cpd.cpd_leverage_sample(h, mode, J, 5)
+    oi, op, near = oc.arls_draw(samplers, mode, J, 77, 5)
+    gi = gi.cpu().numpy()
+    mism = np.any(gi != oi, axis=0)
+    assert not np.any(mism & ~near), "index mismatch away from a tie"
+    ok = ~mism
+    assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-12
+    h.close()
+
+
 def _oracle_samples(fs, mode, J, seed, sweep):
     samplers = [oc.arls_build(U) for U in fs]
     oi, op, _ = oc.arls_draw(samplers, mode, J, seed, sweep)
