@@ -113,13 +113,14 @@ def test_sampled_mttkrp_matches_oracle(cpd, mode):
     h.close()
 
 
-@pytest.mark.parametrize("R,bps", [(8, 0), (128, 1), (128, 8)])
+@pytest.mark.parametrize("R,bps", [(8, 0), (16, 0), (64, 2), (128, 1), (128, 8)])
 def test_sampled_mttkrp_hot_rows(cpd, R, bps):
     """Zipf rows with thousands of nonzeros: rows that the layout marks hot
     are accumulated in shared memory (and, past the slots a launch holds --
     164 hot rows against 105 slots at R = 128 with 8 blocks per SM -- through
     the global path); the result equals the oracle's for every mode, before
-    and after the autotuner changes the launch shape."""
+    and after the autotuner changes the launch shape.  R = 16, 64 and 128 run
+    the kernels compiled for row strides 16, 64 and 128; R = 8 the generic one."""
     dims, nnz, J = (3000, 400, 300), 300_000, 4000
     idx, vals, init = make_case(dims, nnz, R, seed=77, zipf=1.1)
     assert np.bincount(idx[0]).max() > 2000
