@@ -114,6 +114,28 @@ def test_sampled_mttkrp_matches_explicit_sampling_matrix():
         assert np.allclose(got, ref)
 
 
+def test_selected_nnz_matches_brute_force_count():
+    """nnz(mat(T, n) S^T), counted by checking every nonzero against every
+    draw with plain loops (no keys): a nonzero is selected when its indices
+    outside mode n equal those of some draw; repeated draws count once."""
+    rng = np.random.default_rng(12)
+    dims = (7, 5, 6, 3)
+    idx = synth.coo_coordinates(dims, 120, 13)
+    for n in range(4):
+        J = 25
+        sidx = np.stack([rng.integers(0, d, J) for d in dims])
+        sidx[n] = -1
+        sidx[:, 3] = sidx[:, 0]                              # a repeated draw
+        count = 0
+        for e in range(idx.shape[1]):
+            for j in range(J):
+                if all(idx[k, e] == sidx[k, j] for k in range(4) if k != n):
+                    count += 1
+                    break
+        assert oc.selected_nnz(idx, dims, n, sidx) == count
+    assert oc.selected_nnz(idx, dims, 0, np.zeros((4, 0), dtype=np.int64)) == 0
+
+
 def test_sampled_with_every_row_once_equals_exact():
     rng = np.random.default_rng(7)
     dims = (9, 6, 5)
