@@ -229,7 +229,8 @@ cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out);
 
 /*
  * Downsampled MTTKRP without any device allocation (no counterpart in the
- * paper; it restates Eq. 7 for callers that cannot allocate).  Meant for
+ * paper): the same result as cpd_sampled_mttkrp, for callers that cannot
+ * allocate.  Meant for
  * code that must not call cudaMalloc: work enqueued while a stream is being
  * captured into a CUDA graph, code inside a framework whose memory pool
  * already owns the device memory, and latency-bound callers that cannot
@@ -237,13 +238,16 @@ cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out);
  * needs no cpd_handle (creating one allocates): the caller passes the COO
  * tensor and the factor matrices directly, and one pass over the nonzeros
  * picks those whose column was drawn.
- *   N, dims (host), nnz, idx (N x nnz int32), vals    the tensor, as for cpd_create
- *   factors  host array of N device pointers, U_k is I_k x R row-major float32
- *            (row `mode` unused)
+ *   N, dims (host), nnz, idx (N x nnz int32), vals    the tensor, laid out as for
+ *            cpd_create (device memory; repeated coordinates simply add)
+ *   factors  host array of N device pointers, U_k is I_k x R row-major float32;
+ *            factors[mode] is not read and may be NULL
  *   samp_idx N x J int32 drawn KRP rows (row `mode` ignored); w J float64 weights
  *   Y        I_mode x R float32, overwritten
- *   status_out device int32: set to 1 if some draw had an index out of range
- *            (that draw is skipped), else 0
+ *   status_out device int32, written by the GPU: 0 when every index was in
+ *            range, else the OR of 1 (some draw had an index outside [0, I_k):
+ *            that draw is skipped) and 2 (some nonzero had a coordinate
+ *            outside [0, I_k): that nonzero is skipped)
  * Scratch: a fixed 2 MiB table in the library's static device memory, held on
  * every GPU that loads the library until the process exits; J is limited to
  * 65,536 (CPD_ERR_CAPACITY beyond).  The first call on a device looks up the
@@ -285,6 +289,15 @@ void cpd_batch_destroy(cpd_batch b);
  * lanes per draw, leaf rows F}, or NULL.  Synchronises.
  */
 cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices);
+
+/*
+ * STS-CP at precision 0 first scans a leaf's row masses in float32 with a
+ * bound on their rounding error; a draw whose target lies within that bound
+ * of a row boundary has its leaf rescanned in double-float (Sec. 4.1 leaf
+ * scan of Algorithm 5).  *out (host) receives the number of such rescans
+ * since cpd_create (0 for other methods or precision 1).  Synchronises.
+ */
+cpd_status cpd_sts_rescans(cpd_handle h, int64_t* out);
 
 /* Wait for the handle's stream and return the first latched device error. */
 cpd_status cpd_synchronize(cpd_handle h);

@@ -19,7 +19,7 @@ STATUS = {0: "CPD_OK", 1: "CPD_ERR_INVALID_ARG", 2: "CPD_ERR_OUT_OF_RANGE_INDEX"
           8: "CPD_ERR_TIMEOUT", 9: "CPD_ERR_NOT_FINITE"}
 EXPORTS = ["cpd_default_options", "cpd_create", "cpd_leverage_sample", "cpd_sampled_mttkrp", "cpd_exact_mttkrp",
            "cpd_gram_solve", "cpd_als_sweep", "cpd_fit", "cpd_get_factors", "cpd_set_factors", "cpd_get_sigma",
-           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_sampled_mttkrp_noalloc", "cpd_synchronize",
+           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_sampled_mttkrp_noalloc", "cpd_sts_rescans", "cpd_synchronize",
            "cpd_batch_create", "cpd_batch_sweep", "cpd_batch_synchronize", "cpd_batch_destroy", "cpd_autotune",
            "cpd_last_error", "cpd_destroy"]
 PHASES = ["pinv", "draw", "probe", "scan", "spmm", "solve", "gram", "sampler", "exact", "clear"]
@@ -70,6 +70,7 @@ def lib():
         "cpd_profile_read": ([_P, _P, _P], st),
         "cpd_sweep_kernel_count": ([_P, _P], st),
         "cpd_synchronize": ([_P], st),
+        "cpd_sts_rescans": ([_P, _P], st),
         "cpd_batch_create": ([_P, i32, i32, _P, ctypes.POINTER(_P)], st),
         "cpd_batch_sweep": ([_P, i32], st),
         "cpd_batch_synchronize": ([_P], st),
@@ -291,6 +292,13 @@ def cpd_autotune(h):
     out = (ctypes.c_int32 * 3)()
     h._check(lib().cpd_autotune(h.raw, ctypes.cast(out, _P)))
     return out[0], out[1], out[2]
+
+
+def cpd_sts_rescans(h):
+    """Leaves of STS-CP draws rescanned in double-float since creation."""
+    n = ctypes.c_int64()
+    h._check(lib().cpd_sts_rescans(h.raw, ctypes.cast(ctypes.byref(n), _P)))
+    return n.value
 
 
 def cpd_synchronize(h):

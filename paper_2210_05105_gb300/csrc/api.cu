@@ -8,6 +8,7 @@
 #include <cstring>
 
 cpd_status cpd_sts_alloc(cpd_ctx* h);
+cpd_status cpd_sts_fallback_count(cpd_ctx* h, int64_t* out);
 
 // message of the last failed cpd_create on this thread (the handle is gone)
 static thread_local std::string g_create_error;
@@ -496,6 +497,13 @@ cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out) {
   }
   *out = k;
   return CPD_OK;
+}
+
+cpd_status cpd_sts_rescans(cpd_handle h, int64_t* out) {
+  if (!h || !out) return CPD_ERR_INVALID_ARG;
+  cpd_status s = cpd_sts_fallback_count(h, out);
+  if (s != CPD_OK) return s;
+  return read_status(h);
 }
 
 cpd_status cpd_synchronize(cpd_handle h) {

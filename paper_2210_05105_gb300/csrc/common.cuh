@@ -77,10 +77,16 @@ struct cpd_ctx {
   // STS-CP state (Algorithm 4) per factor: heap of 2L node Grams
   int F = 0;
   int64_t L[CPD_MAX_MODES] = {0};
-  float* tree32[CPD_MAX_MODES] = {nullptr};   // 2L x R(R+1)/2 float32 (upper triangles)
+  // node v of factor k's tree at tree[k] + v * tree_stride: the packed upper
+  // triangle (npad floats, R(R+1)/2 padded to 4); with tree_df the node holds
+  // it twice, float32 hi then lo of a double-float (precision 0)
+  float* tree[CPD_MAX_MODES] = {nullptr};
+  bool tree_df = true;
+  int tree_stride = 0;
   double* sts_ggt[CPD_MAX_MODES] = {nullptr}; // R x R: G^+ (*) Grams of factors drawn after k
   double* sts_Z = nullptr;                    // <G^+, G>_F
-  float* sts_h = nullptr;                     // J x Rp running Hadamard products
+  float* sts_h = nullptr;                     // J x Rp running Hadamard products (J x 2Rp hi, lo with tree_df)
+  int* sts_fallbacks = nullptr;               // leaves rescanned in double-float (counter)
   double* sts_q = nullptr;                    // Imax: row masses of the first factor drawn
   double* sts_cdf = nullptr;                  // Imax: their running sums
   double* sts_blk = nullptr;                  // block sums
@@ -266,6 +272,42 @@ __device__ __forceinline__ void df_merge(float& h0, float& l0, float h1, float l
   l0 = __fadd_rn(__fadd_rn(l0, l1), e);
 }
 __device__ __forceinline__ double df_value(float hi, float lo) { return (double)hi + (double)lo; }
+// (hi, lo) := hi + lo renormalised so that |lo| <= ulp(hi) / 2 (Dekker's
+// FastTwoSum; exact when |hi| >= |lo|)
+__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
+// (ah, al) * (bh, bl) to ~2^-46 relative: exact leading product (TwoProduct)
+// plus both cross terms; the lo * lo term is below the result's precision
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  rh = p;
+  rl = e;
+  df_renorm(rh, rl);
+}
+// (ah, al) * b for a float32 b
+__device__ __forceinline__ void df_mul_f(float ah, float al, float b, float& rh, float& rl) {
+  const float p = __fmul_rn(ah, b);
+  rl = __fmaf_rn(al, b, __fmaf_rn(ah, b, -p));
+  rh = p;
+  df_renorm(rh, rl);
+}
+// (sh, sl) += (ah, al) * (bh, bl): the Dot2 step of Ogita, Rump and Oishi
+// with double-float operands (exact leading product, TwoSum into sh, all
+// rounding errors and cross terms gathered in sl)
+__device__ __forceinline__ void df_dot_step(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);
+  float s, e;
+  df_two_sum(sh, p, s, e);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pe))));
+}
 
 #define CPD_STREAM_ARLS 0ull
 #define CPD_STREAM_STS 1ull

@@ -63,7 +63,7 @@ __global__ void na_insert_kernel(NaSlot* __restrict__ table, NaArgs a, const int
       if (i < 0 || (int64_t)i >= a.dims[k]) ok = false;
       key += (unsigned long long)(ok ? i : 0) * a.stride[k];
     }
-    if (!ok) { atomicExch(bad, 1); continue; }
+    if (!ok) { atomicOr(bad, 1); continue; }
     unsigned long long s = cpd_mix64(key) & (NA_SLOTS - 1);
     for (int probe = 0; probe < NA_SLOTS; ++probe) {
       const unsigned long long old = atomicCAS(&table[s].key, CPD_EMPTY64, key);
@@ -78,8 +78,12 @@ __global__ void na_insert_kernel(NaSlot* __restrict__ table, NaArgs a, const int
 
 // One pass over the nonzeros: a nonzero whose column was drawn adds
 // w_col * val * (KRP row) to its output row; a warp takes 32 nonzeros.
+// A nonzero with a coordinate outside [0, I_k) in any mode is skipped and
+// latches bit 1 (value 2) of *bad, so no factor row or output row outside
+// the caller's arrays is ever touched.
 __global__ void na_accumulate_kernel(const NaSlot* __restrict__ table, NaArgs a, const int32_t* __restrict__ idx,
-                                     const float* __restrict__ vals, int64_t nnz, float* __restrict__ Y) {
+                                     const float* __restrict__ vals, int64_t nnz, float* __restrict__ Y,
+                                     int* __restrict__ bad) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -89,7 +93,11 @@ __global__ void na_accumulate_kernel(const NaSlot* __restrict__ table, NaArgs a,
     int32_t ii[CPD_MAX_MODES];
 #pragma unroll
     for (int k = 0; k < CPD_MAX_MODES; ++k) ii[k] = (k < a.N && e < nnz) ? idx[(int64_t)k * nnz + e] : 0;
-    if (e < nnz) {
+    bool in_range = e < nnz;
+    for (int k = 0; k < a.N; ++k)
+      if (ii[k] < 0 || (int64_t)ii[k] >= a.dims[k]) in_range = false;
+    if (e < nnz && !in_range) atomicOr(bad, 2);
+    if (in_range) {
       unsigned long long key = 0;
       for (int k = 0; k < a.N; ++k)
         if (k != a.n) key += (unsigned long long)ii[k] * a.stride[k];
@@ -133,7 +141,7 @@ extern "C" cpd_status cpd_sampled_mttkrp_noalloc(int32_t N, const int64_t* dims,
   long double prod = 1.0L;
   unsigned long long acc = 1;
   for (int k = 0; k < N; ++k) {
-    if (dims[k] < 1 || dims[k] > 0x7fffffffll || !factors[k]) return CPD_ERR_INVALID_ARG;
+    if (dims[k] < 1 || dims[k] > 0x7fffffffll || (k != mode && !factors[k])) return CPD_ERR_INVALID_ARG;
     prod *= (long double)dims[k];
     a.U[k] = factors[k];
     a.dims[k] = dims[k];
@@ -167,7 +175,7 @@ extern "C" cpd_status cpd_sampled_mttkrp_noalloc(int32_t N, const int64_t* dims,
   if (J > 0)
     na_insert_kernel<<<(unsigned)std::min<int64_t>(cpd_ceil_div(J, 256), sms * 4), 256, 0, st>>>(
         table, a, samp_idx, w, J, status_out);
-  if (nnz > 0) na_accumulate_kernel<<<sms * 8, 256, 0, st>>>(table, a, idx, vals, nnz, Y);
+  if (nnz > 0) na_accumulate_kernel<<<sms * 8, 256, 0, st>>>(table, a, idx, vals, nnz, Y, status_out);
   if (cudaGetLastError() != cudaSuccess) return CPD_ERR_CUDA;
   return CPD_OK;
 }

@@ -2,8 +2,10 @@
 callers that cannot call cudaMalloc (code running under stream capture, code
 whose device memory is owned by another allocator, latency-bound callers):
 called through the C ABI, its output must match the handle-based
-cpd_sampled_mttkrp within the 1e-5 relative tolerance of the MTTKRP tests,
-on two calls in a row (the second call sees the first call's table)."""
+cpd_sampled_mttkrp and the FP64 oracle within the 1e-5 relative tolerance of
+the MTTKRP tests, on two calls in a row (the second call sees the first
+call's table).  Out-of-range draws and out-of-range nonzero coordinates are
+skipped and reported in the status word; J = 0 gives Y = 0."""
 import ctypes
 
 import numpy as np
@@ -52,7 +54,66 @@ def test_noalloc_matches_handle_path_twice():
         st, Y, status = _noalloc(cpd, dims, idx_d, vals_d, facs, R, mode, sidx, w)
         assert st == 0 and status == 0, (call, st, status)
         assert rel_frob(Y.cpu().numpy(), Y_ref.cpu().numpy()) <= 1e-5, call
+        Yo = oc.sampled_mttkrp(idx, vals, dims, [f.double().cpu().numpy() for f in facs], mode,
+                               sidx.cpu().numpy(), w.cpu().numpy())
+        assert rel_frob(Y.cpu().numpy(), Yo) <= 1e-5, call
     h.close()
+
+
+def _case():
+    dims, R, J = (60, 50, 40), 6, 500
+    idx, vals, init = make_case(dims, 5000, R, seed=77)
+    rng = np.random.default_rng(78)
+    sidx = np.stack([rng.integers(0, d, J) for d in dims]).astype(np.int32)
+    w = rng.uniform(0.5, 2.0, J)
+    return dims, R, idx, vals, [u.astype(np.float32) for u in init], sidx, w
+
+
+def test_noalloc_out_of_range_draw_is_skipped():
+    cpd = lib_or_build()
+    dims, R, idx, vals, init, sidx, w = _case()
+    mode = 0
+    bad = sidx.copy()
+    bad[1, 7] = dims[1]            # one draw past the end of mode 1
+    facs = [torch.from_numpy(u).cuda() for u in init]
+    st, Y, status = _noalloc(cpd, dims, torch.from_numpy(idx).cuda().contiguous(),
+                             torch.from_numpy(vals).cuda().contiguous(), facs, R, mode,
+                             torch.from_numpy(bad), torch.from_numpy(w))
+    assert st == 0 and status == 1
+    keep = np.ones(w.shape[0], dtype=bool)
+    keep[7] = False
+    Yo = oc.sampled_mttkrp(idx, vals, dims, [u.astype(np.float64) for u in init], mode, sidx[:, keep], w[keep])
+    assert rel_frob(Y.cpu().numpy(), Yo) <= 1e-5
+
+
+def test_noalloc_out_of_range_coordinate_is_skipped():
+    cpd = lib_or_build()
+    dims, R, idx, vals, init, sidx, w = _case()
+    mode = 2
+    # make every nonzero hit a drawn column, then corrupt the mode-n index of one
+    idx = idx.copy()
+    idx[0, :500], idx[1, :500] = sidx[0], sidx[1]
+    clean = oc.sampled_mttkrp(idx[:, 1:], vals[1:], dims, [u.astype(np.float64) for u in init], mode, sidx, w)
+    bad = idx.copy()
+    bad[mode, 0] = dims[mode] + 5
+    facs = [torch.from_numpy(u).cuda() for u in init]
+    facs[mode] = torch.zeros(1, dtype=torch.float32, device="cuda")   # never read
+    st, Y, status = _noalloc(cpd, dims, torch.from_numpy(np.ascontiguousarray(bad)).cuda(),
+                             torch.from_numpy(vals).cuda().contiguous(), facs, R, mode,
+                             torch.from_numpy(sidx), torch.from_numpy(w))
+    assert st == 0 and status == 2
+    assert rel_frob(Y.cpu().numpy(), clean) <= 1e-5
+
+
+def test_noalloc_no_draws_gives_zero():
+    cpd = lib_or_build()
+    dims, R, idx, vals, init, _, _ = _case()
+    facs = [torch.from_numpy(u).cuda() for u in init]
+    st, Y, status = _noalloc(cpd, dims, torch.from_numpy(idx).cuda().contiguous(),
+                             torch.from_numpy(vals).cuda().contiguous(), facs, R, 1,
+                             torch.zeros((3, 0), dtype=torch.int32), torch.zeros(0, dtype=torch.float64))
+    assert st == 0 and status == 0
+    assert float(Y.abs().max()) == 0.0
 
 
 def test_noalloc_rejects_oversized_sample_lists():
