@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="batched workloads: keep the default launch shapes")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-parity", action="store_true", help="skip the oracle parity block of the JSON line")
     p.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -166,6 +167,81 @@ def cpu_worker(path):
         oc.als_mode_update(state, n, meta["method"], meta["J"], meta["seed"], 0)
     dt = time.perf_counter() - t0
     print(json.dumps({"seconds": dt, "mode_updates": len(modes)}))
+
+
+def parity_check(cpd, h, w, method, idx_np, vals_np, sweep_id, leaf_rows=0, sts_draws=8192):
+    """Step-wise parity of the GPU against the FP64 oracle after the timed
+    sweeps, from the GPU's current model: the fit formula (Sec. 5.1) on the
+    GPU's factors, one mode update's draws (index matches, oracle near-ties
+    at 1e-12), the downsampled MTTKRP on the GPU's draws (Eq. 7, relative
+    Frobenius error and selected-nonzero count) and the solve (Eq. 4)."""
+    import torch
+    from oracle import cpals as oc
+    dims, R, J = w["dims"], w["R"], w["J"]
+    N = len(dims)
+    mode = 1 % N
+    t0 = time.perf_counter()
+    fs = [cpd.cpd_get_factors(h, k).double().cpu().numpy() for k in range(N)]
+    sigma = cpd.cpd_get_sigma(h).cpu().numpy()
+    fit_gpu = cpd.cpd_fit(h)
+    fit_or = oc.fit(idx_np, vals_np, fs, sigma)
+    out = {"kind": "one mode update of the oracle from the GPU's factors after the timed sweeps", "mode": mode,
+           "fit_gpu": fit_gpu, "fit_oracle": fit_or, "fit_gap": abs(fit_gpu - fit_or)}
+    if method == "exact":
+        Y = cpd.cpd_exact_mttkrp(h, mode)
+        Yo = oc.exact_mttkrp(idx_np, vals_np, dims, fs, mode)
+        out["mttkrp_rel_err"] = float(np.linalg.norm(Y.double().cpu().numpy() - Yo) / np.linalg.norm(Yo))
+    else:
+        Jd = J if method == "arls" else min(J, sts_draws)
+        gi, gp = cpd.cpd_leverage_sample(h, mode, Jd, sweep_id)
+        if method == "arls":
+            oi, op, near = oc.arls_draw([oc.arls_build(U) for U in fs], mode, Jd, w["sample_seed"], sweep_id)
+        else:
+            oi, op, near = oc.sts_draw([oc.sts_build(U, leaf_rows or R) for U in fs], fs, [oc.gram(U) for U in fs],
+                                       mode, Jd, w["sample_seed"], sweep_id)
+        gi_np = gi.cpu().numpy()
+        mism = np.any(gi_np != oi, axis=0)
+        ok = ~mism
+        gp_np = gp.cpu().numpy()
+        wts = 1.0 / (Jd * gp)
+        Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, gi, wts)
+        Yg = Y.double().cpu().numpy()
+        Yo = oc.sampled_mttkrp(idx_np, vals_np, dims, fs, mode, gi_np, wts.cpu().numpy())
+        out.update({"draws": Jd, "index_match": int(ok.sum()), "ties": int(near.sum()),
+                    "differ_away_from_tie": int((mism & ~near).sum()),
+                    "prob_max_rel_err": float(np.max(np.abs(gp_np[ok] - op[ok]) / op[ok])) if ok.any() else None,
+                    "mttkrp_rel_err": float(np.linalg.norm(Yg - Yo) / np.linalg.norm(Yo)),
+                    "nnz_sel_gpu": nsel, "nnz_sel_oracle": oc.selected_nnz(idx_np, dims, mode, gi_np)})
+    G = oc.hadamard_of_grams([oc.gram(U) for U in fs], mode)
+    Un, _ = oc.solve_and_renorm(Y.double().cpu().numpy(), oc.pinv_sym(G))
+    cpd.cpd_gram_solve(h, mode, Y)
+    Ug = cpd.cpd_get_factors(h, mode).double().cpu().numpy()
+    out["solve_rel_err"] = float(np.linalg.norm(Ug - Un) / np.linalg.norm(Un))
+    out["seconds"] = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    return out
+
+
+def small_fit_parity(method):
+    """Whole-run parity on the 200 x 150 x 100 workload (2e4 nonzeros, R = 8,
+    J = 2000): 5 ALS rounds on the GPU and in the FP64 oracle from the same
+    inputs and uniforms, final fits compared."""
+    import torch
+    from oracle import cpals as oc
+    from paper_2210_05105_gb300 import cpd
+    w = synth.WORKLOADS["small_uniform_200x150x100"]
+    dims, R, J, S = w["dims"], w["R"], w["J"], w["sweeps"]
+    idx, vals = synth.make_tensor(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"])
+    init = synth.init_factors(dims, R, w["init_seed"])
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method=method, rank=R, samples=J,
+                       seed=w["sample_seed"])
+    cpd.cpd_als_sweep(h, S)
+    f_gpu = cpd.cpd_fit(h)
+    h.close()
+    _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], method, S, J=J, seed=w["sample_seed"])
+    return {"workload": "small_uniform_200x150x100", "sweeps": S, "fit_gpu": f_gpu, "fit_oracle": fits[-1],
+            "fit_gap": abs(f_gpu - fits[-1])}
 
 
 def run_oracle(idx, vals, init, w, method, modes, threads=1):
@@ -393,17 +469,31 @@ def ours(args, world, rank, local):
                "d2h_bytes_per_step": d2h / args.steps, "job": "cpd_create(host COO) + %d sweeps + fit + factors to host"
                % args.steps, "job_seconds": e2e_s, "fit": f2}
 
-    cpu = None
+    cpu = cpu1 = None
+    idx_np = vals_np = None
     if not args.no_cpu and rank == 0 and w["nnz"] > ORACLE_MAX_NNZ:
         cpu = {"value": None, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
                "sample": "not run: the oracle's per-mode layout build of %d nonzeros in host memory exceeds the "
                          "bounded sample this bench allows" % w["nnz"]}
     elif not args.no_cpu and rank == 0:
         idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
-        res = run_oracle(idx_np, vals_np, init_np, w, args.method, list(range(N)))
-        cpu = {"value": (res["mode_updates"] / N) / res["seconds"], "unit": "sweeps/s", "cores": 1,
-               "kind": "oracle", "sample": "one ALS round (all %d mode updates) of the full workload, FP64 numpy, "
-                                          "1 thread, from the initial factors" % N, "seconds": res["seconds"]}
+        ncpu = os.cpu_count() or 1
+        res = run_oracle(idx_np, vals_np, init_np, w, args.method, list(range(N)), threads=ncpu)
+        res1 = run_oracle(idx_np, vals_np, init_np, w, args.method, list(range(N)), threads=1)
+        cpu = {"value": (res["mode_updates"] / N) / res["seconds"], "unit": "sweeps/s", "cores": ncpu,
+               "kind": "oracle", "sample": "one ALS round (all %d mode updates) of the full workload, FP64 numpy "
+                                          "with %d BLAS threads (numpy's elementwise steps stay on one core), "
+                                          "from the initial factors" % (N, ncpu), "seconds": res["seconds"]}
+        cpu1 = {"value": (res1["mode_updates"] / N) / res1["seconds"], "unit": "sweeps/s", "cores": 1,
+                "kind": "oracle", "sample": "the same ALS round, 1 thread", "seconds": res1["seconds"]}
+    parity = None
+    if not args.no_parity and rank == 0:
+        if idx_np is None:
+            idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
+        parity = parity_check(cpd, h, w, args.method, idx_np, vals_np, args.warmup + args.steps + 1,
+                              leaf_rows=args.leaf_rows)
+        if args.workload != "small_uniform_200x150x100":
+            parity["small_workload_run"] = small_fit_parity(args.method)
     h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
@@ -416,7 +506,8 @@ def ours(args, world, rank, local):
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MB write, outside the events)",
                            "create_seconds": create_s},
-                "roofline": roofline, "roofline_spmm": roofline_spmm, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "roofline_spmm": roofline_spmm, "cpu_baseline": cpu,
+                "cpu_baseline_1core": cpu1, "parity": parity, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "phases_ms_per_sweep": {k: round(v[0], 4) for k, v in phases.items() if v[1]},
                 "mttkrp_stats_per_mode": {k: stats[k] for k in ("nnz_sel", "J_u", "rows")},

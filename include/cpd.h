@@ -53,7 +53,8 @@ typedef enum {
   CPD_ERR_OOM = 4,               /* device allocation failed */
   CPD_ERR_CUDA = 5,              /* a CUDA runtime call failed; see cpd_last_error */
   CPD_ERR_CAPACITY = 6,          /* more samples / selected nonzeros than allocated */
-  CPD_ERR_SINGULAR_GRAM = 7,     /* reserved: pseudo-inverse failed to converge */
+  CPD_ERR_SINGULAR_GRAM = 7,     /* no pseudo-inverse of a Gram (Eq. 4): its eigensolver
+                                    did not converge, i.e. the Gram held NaN or Inf */
   CPD_ERR_TIMEOUT = 8,           /* a bounded device-side wait gave up */
   CPD_ERR_NOT_FINITE = 9         /* NaN or Inf in values or factors */
 } cpd_status;
@@ -104,7 +105,12 @@ cpd_status cpd_default_options(cpd_options* opt);
  *   idx           N x nnz int32, mode-major (idx[k * nnz + e] = i_k of nonzero e).
  *   vals          nnz float32.
  *   init_factors  concatenated U_0 .. U_{N-1}, each I_k x R row-major float32
- *                 (the N(0,1) draws of Algorithm 1 line 1); must not be NULL.
+ *                 (the N(0,1) draws of Algorithm 1 line 1), or NULL: the library
+ *                 draws U_k[i, r] itself by the Box-Muller transform of two
+ *                 uniforms from Philox4x64-10 with key (seed, 2) and counter
+ *                 (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53,
+ *                 u2 = top 53 bits of word 1 times 2^-53,
+ *                 z = sqrt(-2 ln u1) cos(2 pi u2) in float64, rounded to float32.
  *   cuda_stream   cudaStream_t the handle enqueues on (NULL: legacy stream).
  * The library copies and re-sorts the inputs (one layout per matricization,
  * sorted by KRP-row key, with a hash index from key to its nonzeros, Sec. 4.3)

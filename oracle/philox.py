@@ -92,3 +92,25 @@ def draw_uniforms(seed, stream, j, k, n, s):
 # stream ids of the key's second word, one per use of randomness in the method
 STREAM_ARLS = 0
 STREAM_STS = 1
+STREAM_INIT = 2
+
+
+def gaussian_factors(dims, R, seed):
+    """Unit-variance Gaussian factors of Algorithm 1 line 1 drawn from the
+    same generator: entry (i, r) of U_k is the Box-Muller transform (Box and
+    Muller, 1958) of two uniforms from Philox4x64-10 with key (seed, 2) and
+    counter (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53 in (0, 1],
+    u2 = top 53 bits of word 1 times 2^-53, z = sqrt(-2 ln u1) cos(2 pi u2)
+    in binary64, rounded to float32.  Returns a list of (I_k, R) float32."""
+    out = []
+    for k, I in enumerate(dims):
+        i = np.repeat(np.arange(int(I), dtype=np.uint64), R)
+        r = np.tile(np.arange(R, dtype=np.uint64), int(I))
+        ctr = [i, r, np.full(i.shape, k, dtype=np.uint64), np.zeros(i.shape, dtype=np.uint64)]
+        key = [np.full(i.shape, seed, dtype=np.uint64), np.full(i.shape, STREAM_INIT, dtype=np.uint64)]
+        w = philox4x64(ctr, key)
+        u1 = ((w[0] >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * (2.0 ** -53)
+        u2 = (w[1] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+        out.append(z.astype(np.float32).reshape(int(I), R))
+    return out

@@ -118,16 +118,19 @@ def cpd_create(dims, idx, vals, init_factors, method="arls", rank=8, samples=200
                stream=None, sketched_gram=False, fast=False, spmm_blocks_per_sm=0, sum_duplicates=False):
     """Build a handle.  idx (N, nnz) int32, vals (nnz,) float32 and the init
     factors (list of (I_k, R) float32) must all be on the same device: all
-    CUDA, or all CPU (then they are copied by the library, host input)."""
+    CUDA, or all CPU (then they are copied by the library, host input).
+    init_factors=None lets the library draw the N(0, 1) initial factors from
+    the seed."""
     L = lib()
     dims = [int(d) for d in dims]
     N = len(dims)
     on_host = not idx.is_cuda
     idx = idx.contiguous()
     vals = vals.contiguous()
-    init = torch.cat([u.reshape(-1) for u in init_factors]).contiguous()
+    init = None if init_factors is None else torch.cat([u.reshape(-1) for u in init_factors]).contiguous()
     if on_host:
-        idx, vals, init = idx.pin_memory(), vals.pin_memory(), init.pin_memory()
+        idx, vals = idx.pin_memory(), vals.pin_memory()
+        init = None if init is None else init.pin_memory()
     opt = cpd_options()
     L.cpd_default_options(ctypes.byref(opt))
     opt.method = METHODS[method] if isinstance(method, str) else int(method)

@@ -49,6 +49,25 @@ __global__ void fill_kernel(double* p, int n, double v) {
 
 __global__ void bump_kernel(unsigned long long* ctr) { *ctr += 1ull; }
 
+// Algorithm 1 line 1 when the caller passes no initial factors: U_k[i, r]
+// ~ N(0, 1) by the Box-Muller transform of two uniforms from Philox4x64-10,
+// key (seed, 2), counter (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53
+// in (0, 1], u2 = top 53 bits of word 1 times 2^-53,
+// z = sqrt(-2 ln u1) cos(2 pi u2) in float64, rounded to float32.
+__global__ void gauss_init_kernel(float* __restrict__ U, int64_t I, int R, int Rp, int k, unsigned long long seed) {
+  const int64_t n = I * R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / R;
+    const int r = (int)(e - i * R);
+    unsigned long long c[4] = {(unsigned long long)i, (unsigned long long)r, (unsigned long long)k, 0ull};
+    cpd_philox4x64(c, seed, CPD_STREAM_INIT);
+    const double u1 = (double)((c[0] >> 11) + 1ull) * 0x1.0p-53;
+    const double u2 = (double)(c[1] >> 11) * 0x1.0p-53;
+    const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+    U[i * Rp + r] = (float)z;
+  }
+}
+
 // One mode update of Algorithm 1 (lines 6-8) on the handle's stream.
 // Pseudo-inverse of the Hadamard product of Grams for `mode` on the forked
 // side stream of a captured sweep (it depends only on the factor Grams, so it
@@ -185,8 +204,14 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   }
   int64_t off = 0;
   for (int k = 0; k < N; ++k) {
-    CPD_CUDA(h, cudaMemcpy2DAsync(h->U[k], (size_t)Rp * sizeof(float), init + off, (size_t)R * sizeof(float),
-                                  (size_t)R * sizeof(float), (size_t)dims[k], kind, st));
+    if (init) {
+      CPD_CUDA(h, cudaMemcpy2DAsync(h->U[k], (size_t)Rp * sizeof(float), init + off, (size_t)R * sizeof(float),
+                                    (size_t)R * sizeof(float), (size_t)dims[k], kind, st));
+    } else {
+      const int g = (int)std::min<int64_t>(cpd_ceil_div(dims[k] * R, 256), (int64_t)h->num_sms * 8);
+      gauss_init_kernel<<<g, 256, 0, st>>>(h->U[k], dims[k], R, Rp, k, h->opt.seed);
+      CPD_LAUNCH(h, "gauss_init");
+    }
     off += dims[k] * R;
   }
   if ((s = cpd_alloc(h, &h->sigma, (size_t)R)) != CPD_OK) return s;
@@ -284,7 +309,7 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
   if (!opt || !dims || N < 1 || N > CPD_MAX_MODES || nnz < 0 || nnz >= 0xffffffffll) return CPD_ERR_INVALID_ARG;
   if (opt->rank < 1 || opt->rank > CPD_MAX_RANK || opt->samples < 0) return CPD_ERR_INVALID_ARG;
   if (opt->method < CPD_ARLS_LEV || opt->method > CPD_EXACT) return CPD_ERR_INVALID_ARG;
-  if (!init_factors || (nnz > 0 && (!idx || !vals))) return CPD_ERR_INVALID_ARG;
+  if (nnz > 0 && (!idx || !vals)) return CPD_ERR_INVALID_ARG;
   if (opt->method != CPD_EXACT && opt->samples < 1) return CPD_ERR_INVALID_ARG;
   {
     const int b = opt->spmm_blocks_per_sm;

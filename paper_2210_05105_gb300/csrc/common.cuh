@@ -311,6 +311,7 @@ __device__ __forceinline__ void df_dot_step(float& sh, float& sl, float ah, floa
 
 #define CPD_STREAM_ARLS 0ull
 #define CPD_STREAM_STS 1ull
+#define CPD_STREAM_INIT 2ull
 
 // ---- launchers implemented across the .cu files --------------------------
 // layout.cu

@@ -185,6 +185,7 @@ struct PinvJob {
   double* out_pinv;
   float* out_split;                 // may be null: out_pinv as float32 hi (R x R) then lo (R x R)
   double* scratch;                  // 2 R x R float64 (global)
+  int* status;                      // latched CPD_ERR_SINGULAR_GRAM if the eigensolver fails
 };
 struct PinvJobs { PinvJob job[2]; };
 
@@ -445,6 +446,7 @@ __device__ __forceinline__ bool pinv_body(const PinvJob& jb, int R, int fast) {
   const int Re = R + (R & 1);
   const int npair = Re / 2;
   const double eps = 2.220446049250313e-16;
+  bool converged = false;
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int e = t; e < RR; e += nt) {
@@ -453,7 +455,7 @@ __device__ __forceinline__ bool pinv_body(const PinvJob& jb, int R, int fast) {
     }
     off = block_sum_d(off, red);
     dg = block_sum_d(dg, red);
-    if (off <= ((double)R * eps) * ((double)R * eps) * dg) break;
+    if (off <= ((double)R * eps) * ((double)R * eps) * dg) { converged = true; break; }   // uniform
     for (int rnd = 0; rnd < Re - 1; ++rnd) {
       if (t < npair) {
         int i = t;
@@ -503,6 +505,10 @@ __device__ __forceinline__ bool pinv_body(const PinvJob& jb, int R, int fast) {
       __syncthreads();
     }
   }
+  // 60 cyclic sweeps converge quadratically for any finite symmetric
+  // matrix; not converging means non-finite entries (a NaN or Inf reached
+  // the Grams): no pseudo-inverse exists
+  if (!converged && t == 0 && jb.status) cpd_set_status(jb.status, CPD_ERR_SINGULAR_GRAM);
   double lmax = 0.0;
   for (int a = 0; a < R; ++a) lmax = fmax(lmax, fabs(A[a * R + a]));
   const double cut = (double)R * 0x1.0p-52 * lmax;
@@ -865,6 +871,7 @@ cpd_status cpd_hadamard_pinv(cpd_ctx* h, int mode, double* Gout, double* Pout, d
   j.out_pinv = Pout;
   j.out_split = Pout == h->Gnpinv ? h->Gnpinv_split : nullptr;
   j.scratch = scratch ? scratch : h->Gpart;   // 2 R^2 doubles
+  j.status = h->status;
   return launch_pinv(h, jobs, 1);
 }
 
@@ -876,6 +883,7 @@ cpd_status cpd_pinv_into(cpd_ctx* h, const double* G, double* P) {
   jobs.job[0].out_pinv = P;
   jobs.job[0].out_split = P == h->Gnpinv ? h->Gnpinv_split : nullptr;
   jobs.job[0].scratch = h->Gpart;
+  jobs.job[0].status = h->status;
   return launch_pinv(h, jobs, 1);
 }
 

@@ -57,7 +57,8 @@ def test_default_options_and_argument_errors(cpd):
     assert L.cpd_default_options(None) == 1
     out = ctypes.c_void_p()
     dims = (ctypes.c_int64 * 3)(4, 4, 4)
-    # N = 0, rank out of range, missing init: rejected before touching CUDA
+    # N = 0, rank out of range, nonzeros without indices: rejected before
+    # touching CUDA (a NULL init_factors is valid: the library draws them)
     assert L.cpd_create(0, ctypes.cast(dims, ctypes.c_void_p), 0, None, None, None, ctypes.byref(opt), None,
                         ctypes.byref(out)) == 1
     bad = cpd.cpd_options()
@@ -65,7 +66,7 @@ def test_default_options_and_argument_errors(cpd):
     bad.rank = 129
     assert L.cpd_create(3, ctypes.cast(dims, ctypes.c_void_p), 0, None, None, None, ctypes.byref(bad), None,
                         ctypes.byref(out)) == 1
-    assert L.cpd_create(3, ctypes.cast(dims, ctypes.c_void_p), 0, None, None, None, ctypes.byref(opt), None,
+    assert L.cpd_create(3, ctypes.cast(dims, ctypes.c_void_p), 5, None, None, None, ctypes.byref(opt), None,
                         ctypes.byref(out)) == 1
     assert out.value is None
     assert L.cpd_als_sweep(None, 1) == 1

@@ -80,6 +80,25 @@ def test_fullsize_sampled_mttkrp_and_solve(full):
     assert np.max(np.abs(sigma - sig_ref) / sig_ref) <= 1e-5
 
 
+def test_fullsize_three_round_fit_matches_oracle(full):
+    """Three whole ALS rounds of CP-ARLS-LEV at the full size from the same
+    initial factors and uniforms: the GPU's fit and the FP64 oracle's agree
+    to 1e-3 (the draws are decided on float64 scores on both sides, so the
+    trajectories differ only by the float32 rounding of the factors)."""
+    cpd, _, idx, vals = full
+    dims, R, J = W["dims"], W["R"], W["J"]
+    init = synth.init_factors(dims, R, W["init_seed"])
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J,
+                       seed=W["sample_seed"])
+    cpd.cpd_als_sweep(h, 3)
+    f_gpu = cpd.cpd_fit(h)
+    h.close()
+    _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], "arls", 3, J=J, seed=W["sample_seed"])
+    print("full-size 3-round fit: GPU %.6f oracle %.6f gap %.2e" % (f_gpu, fits[-1], abs(f_gpu - fits[-1])))
+    assert abs(f_gpu - fits[-1]) < 1e-3
+
+
 def test_fullsize_sts_draws_match_oracle(full):
     """STS-CP at the full size (leaf rows F = R = 32, a 12-level tree per
     factor), in the launch configuration of `bench.py --method sts`: all

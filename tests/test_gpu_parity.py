@@ -494,3 +494,41 @@ def test_duplicate_coordinates_summed_on_request(cpd):
         fo = oc.fit(uidx, uvals, fs, cpd.cpd_get_sigma(h).cpu().numpy())
         assert abs(f - fo) < 1e-9
         h.close()
+
+
+def test_library_drawn_initial_factors_match_oracle_generator(cpd):
+    """init_factors = NULL: the library draws U_k ~ N(0, 1) from the seed
+    (Box-Muller on Philox4x64-10, key (seed, 2)); after the normalisation of
+    Algorithm 1 line 2 they equal the oracle's draws from the same
+    definition to float32 rounding, and the handle then runs as if the caller
+    had passed those factors."""
+    from oracle import philox as ph
+    dims, R, J, seed = (230, 170, 90), 8, 1500, 4242
+    idx, vals, _ = make_case(dims, 15000, R, seed=55)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(), None, method="arls",
+                       rank=R, samples=J, seed=seed)
+    init = ph.gaussian_factors(dims, R, seed)
+    for k in range(3):
+        got = cpd.cpd_get_factors(h, k).double().cpu().numpy()
+        ref = oc.renormalize(init[k].astype(np.float64))
+        assert np.max(np.abs(got - ref)) < 1e-6, k
+    h2 = create(cpd, dims, idx, vals, init, "arls", R, J, seed=seed)
+    cpd.cpd_als_sweep(h, 2)
+    cpd.cpd_als_sweep(h2, 2)
+    assert abs(cpd.cpd_fit(h) - cpd.cpd_fit(h2)) < 1e-6
+    h.close()
+    h2.close()
+
+
+def test_non_finite_gram_reports_singular_gram(cpd):
+    """A NaN that reaches a Gram leaves Eq. 4 without a pseudo-inverse: the
+    eigensolver does not converge and CPD_ERR_SINGULAR_GRAM is latched and
+    returned by the next synchronising call."""
+    h, idx, vals, init, cfg = _small(cpd)
+    Y = torch.ones((cfg["dims"][1], cfg["R"]), dtype=torch.float32, device="cuda")
+    Y[3, 2] = float("nan")
+    with pytest.raises(cpd.CpdError) as ei:
+        cpd.cpd_gram_solve(h, 1, Y)
+    assert ei.value.status == 7
+    h.close()
+

@@ -51,6 +51,27 @@ def test_uniform_mapping_range_and_resolution():
     assert abs(us.mean() - 0.5) < 5e-3 and abs(us.var() - 1 / 12) < 2e-3
 
 
+def test_gaussian_factors_follow_the_normal_law():
+    """Library-side initial factors (Algorithm 1 line 1): the Box-Muller
+    transform of the Philox uniforms is N(0, 1) -- Kolmogorov-Smirnov against
+    the normal CDF of scipy, first four moments, no infinities (u1 > 0) --
+    and distinct factors, rows and columns get distinct counters."""
+    from scipy import stats
+    fs = ph.gaussian_factors((700, 300), 200, seed=5)
+    z = np.concatenate([f.ravel() for f in fs]).astype(np.float64)
+    assert np.all(np.isfinite(z)) and z.shape[0] == 200000
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 0.012 and abs(z.var() - 1.0) < 0.012
+    assert abs(stats.skew(z)) < 0.03 and abs(stats.kurtosis(z)) < 0.06
+    # columns are uncorrelated and the same seed reproduces the same draws
+    c = np.corrcoef(fs[0][:, :20].T)
+    assert np.max(np.abs(c - np.eye(20))) < 0.2
+    again = ph.gaussian_factors((700, 300), 200, seed=5)
+    assert all((a == b).all() for a, b in zip(fs, again))
+    other = ph.gaussian_factors((700, 300), 200, seed=6)
+    assert not np.array_equal(fs[0], other[0])
+
+
 def test_pinv_against_svd_and_penrose_conditions():
     rng = np.random.default_rng(3)
     for R, rank in [(6, 6), (8, 5), (12, 3)]:
