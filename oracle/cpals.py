@@ -179,9 +179,10 @@ def selected_nnz(idx, dims, n, samp_idx):
 # ---------------------------------------------------------------------------
 
 def leverage_scores(U, Gk_pinv):
-    """dist_k = diag(U_k G_k^+ U_k^T) (Algorithm 2 line 2, Eq. 8 on one factor)."""
+    """dist_k = diag(U_k G_k^+ U_k^T) (Algorithm 2 line 2, Eq. 8 on one factor):
+    row i is the dot product of row i of U_k G_k^+ with row i of U_k."""
     U = np.asarray(U, dtype=np.float64)
-    return np.einsum("ia,ab,ib->i", U, Gk_pinv, U)
+    return np.sum((U @ np.asarray(Gk_pinv, dtype=np.float64)) * U, axis=1)
 
 
 def arls_build(U):
