@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-parity", action="store_true", help="skip the oracle parity block of the JSON line")
     p.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-large", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -220,6 +221,119 @@ def parity_check(cpd, h, w, method, idx_np, vals_np, sweep_id, leaf_rows=0, sts_
     out["seconds"] = time.perf_counter() - t0
     torch.cuda.synchronize()
     return out
+
+
+def parity_check_large(cpd, h, w, method, idx, vals, sweep_id, nrows=512):
+    """Parity of one mode update at a size where the oracle cannot take the
+    whole tensor (the billion-scale workload): the oracle's CP-ARLS-LEV draws
+    from the GPU's factors (all J; Algorithm 3), and the downsampled MTTKRP
+    (Eq. 7) and the solve (Eq. 4) on `nrows` random output rows, whose
+    nonzeros are picked out of the device COO with torch.  STS-CP draws and
+    the fit are not compared here: the oracle's tree of 2^18 node Grams of
+    R x R float64 and its dense per-nonzero model matrix do not fit a bounded
+    sample."""
+    import torch
+    from oracle import cpals as oc
+    dims, R, J = w["dims"], w["R"], w["J"]
+    N = len(dims)
+    mode = 1 % N
+    t0 = time.perf_counter()
+    fs = [cpd.cpd_get_factors(h, k).double().cpu().numpy() for k in range(N)]
+    out = {"kind": "one mode update of the oracle from the GPU's factors after the timed sweeps; MTTKRP and solve "
+                   "on %d random output rows" % nrows, "mode": mode, "fit_gpu": cpd.cpd_fit(h), "fit_oracle": None}
+    if method == "arls":
+        gi, gp = cpd.cpd_leverage_sample(h, mode, J, sweep_id)
+        oi, op, near = oc.arls_draw([oc.arls_build(U) if k != mode else {"C": 1.0, "cdf": np.ones(1), "ell": np.ones(1)}
+                                     for k, U in enumerate(fs)], mode, J, w["sample_seed"], sweep_id)
+        gi_np = gi.cpu().numpy()
+        mism = np.any(gi_np != oi, axis=0)
+        ok = ~mism
+        gp_np = gp.cpu().numpy()
+        out.update({"draws": J, "index_match": int(ok.sum()), "ties": int(near.sum()),
+                    "differ_away_from_tie": int((mism & ~near).sum()),
+                    "prob_max_rel_err": float(np.max(np.abs(gp_np[ok] - op[ok]) / op[ok])) if ok.any() else None})
+    else:
+        gi, gp = cpd.cpd_leverage_sample(h, mode, J, sweep_id)
+        gi_np = gi.cpu().numpy()
+    wts = 1.0 / (J * gp)
+    Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, gi, wts)
+    rng = np.random.default_rng(99)
+    rows = np.sort(rng.choice(dims[mode], size=min(nrows, dims[mode]), replace=False))
+    rows_t = torch.from_numpy(rows).to(idx.device)
+    sel = torch.isin(idx[mode].long(), rows_t)
+    sub_idx = idx[:, sel].cpu().numpy()
+    sub_vals = vals[sel].cpu().numpy()
+    Yo = oc.sampled_mttkrp(sub_idx, sub_vals, dims, fs, mode, gi_np, wts.cpu().numpy())[rows]
+    Yg = Y.double().cpu().numpy()
+    out.update({"mttkrp_rows": int(rows.size), "mttkrp_rows_nonzeros": int(sub_vals.size),
+                "mttkrp_rel_err": float(np.linalg.norm(Yg[rows] - Yo) / np.linalg.norm(Yo)) if np.any(Yo) else 0.0,
+                "nnz_sel_gpu": nsel})
+    G = oc.hadamard_of_grams([oc.gram(U) for U in fs], mode)
+    Un, _ = oc.solve_and_renorm(Yg, oc.pinv_sym(G))
+    cpd.cpd_gram_solve(h, mode, Y)
+    Ug = cpd.cpd_get_factors(h, mode).double().cpu().numpy()
+    out["solve_rel_err"] = float(np.linalg.norm(Ug[rows] - Un[rows]) / np.linalg.norm(Un[rows]))
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def cpu_worker_large(path):
+    """Time pieces of one oracle ALS round on bounded samples of a workload too
+    large for the oracle as a whole, and extrapolate linearly: the downsampled
+    MTTKRP of mode 0 on the first S nonzeros (x nnz / S, x N modes), the
+    CP-ARLS-LEV sampler build and the solve on the first m rows of the largest
+    factor (x the total rows of all factors)."""
+    from oracle import cpals as oc
+    d = np.load(path, allow_pickle=True)
+    meta = json.loads(str(d["meta"]))
+    dims, R, nnz = meta["dims"], meta["R"], meta["nnz"]
+    N = len(dims)
+    idx, vals = d["idx"], d["vals"]
+    factors = [np.load(path + ".f%d.npy" % k, mmap_mode="r") if k != 0 else np.zeros((1, R)) for k in range(N)]
+    factors = [np.asarray(f, dtype=np.float64) for f in factors]
+    t0 = time.perf_counter()
+    oc.sampled_mttkrp(idx, vals, dims, factors, 0, d["samp_idx"], d["w"])
+    t_mttkrp = time.perf_counter() - t0
+    big = int(np.argmax(dims))
+    m = int(meta["rows"])
+    U = np.asarray(np.load(path + ".f%d.npy" % big, mmap_mode="r")[:m], dtype=np.float64)
+    t0 = time.perf_counter()
+    st = oc.arls_build(U)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oc.solve_and_renorm(U, st["Gpinv"])
+    t_solve = time.perf_counter() - t0
+    S = idx.shape[1]
+    round_s = N * t_mttkrp * (nnz / S) + (t_build + t_solve) * (sum(dims) / m)
+    print(json.dumps({"seconds": round_s, "t_mttkrp_sample": t_mttkrp, "nnz_sample": S, "t_build": t_build,
+                      "t_solve": t_solve, "rows_sample": m}))
+
+
+def run_oracle_large(idx_h, vals_h, samp, w, threads, S=20_000_000, rows=400_000):
+    samp_idx, wts, fs = samp
+    dims = w["dims"]
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "case.npz")
+        meta = {"dims": list(dims), "R": w["R"], "nnz": w["nnz"], "rows": rows}
+        np.savez(path, idx=idx_h[:, :S].numpy(), vals=vals_h[:S].numpy(), samp_idx=samp_idx, w=wts,
+                 meta=json.dumps(meta))
+        for k, f in enumerate(fs):
+            np.save(path + ".f%d.npy" % k, f)
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", path, "--cpu-large"], env=env,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr[-2000:])
+        res = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": 1.0 / res["seconds"], "unit": "sweeps/s", "cores": threads, "kind": "oracle",
+            "extrapolated": True, "seconds": res["seconds"],
+            "sample": "extrapolated ALS round: the oracle's downsampled MTTKRP of mode 0 on the first %d nonzeros "
+                      "with the GPU's %d draws (%.2f s, x nnz / %d x %d modes) plus its CP-ARLS-LEV sampler build and "
+                      "solve on %d rows of the largest factor (x all rows); FP64 numpy, %d BLAS threads"
+                      % (S, w["J"], res["t_mttkrp_sample"], S, len(dims), rows, threads)}
 
 
 def small_fit_parity(method):
@@ -389,10 +503,20 @@ def ours(args, world, rank, local):
     w = workload(args)
     dims, R, J = w["dims"], w["R"], w["J"]
     N = len(dims)
-    idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
-    init_np = synth.init_factors(dims, R, w["init_seed"])
-    init = [torch.from_numpy(u).cuda() for u in init_np]
+    gen_s = draws_used = None
+    t0 = time.perf_counter()
+    if w.get("generator") == "device":
+        # billion-scale: coordinates drawn on the device, N(0, 1) initial
+        # factors drawn by the library from the seed (init_factors = NULL)
+        idx, vals, draws_used = synth.make_tensor_device(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"])
+        init_np, init = None, None
+    else:
+        idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
+        init_np = synth.init_factors(dims, R, w["init_seed"])
+        init = [torch.from_numpy(u).cuda() for u in init_np]
     torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    large = w["nnz"] > ORACLE_MAX_NNZ
     t0 = time.perf_counter()
     h = cpd.cpd_create(dims, idx, vals, init, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
                        sketched_gram=args.sketched, fast=args.fast, leaf_rows=args.leaf_rows)
@@ -446,12 +570,38 @@ def ours(args, world, rank, local):
         roofline["traffic"] = TRAFFIC_BYTES.get((args.workload, args.method, roofline["phase"]))
     roofline_spmm = roofline
 
+    # parity against the FP64 oracle from the GPU's model after the timed sweeps
+    parity = None
+    idx_np = vals_np = None
+    if not args.no_parity and rank == 0:
+        if large:
+            parity = parity_check_large(cpd, h, w, args.method, idx, vals, args.warmup + args.steps + 1)
+        else:
+            idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
+            parity = parity_check(cpd, h, w, args.method, idx_np, vals_np, args.warmup + args.steps + 1,
+                                  leaf_rows=args.leaf_rows)
+            if args.workload != "small_uniform_200x150x100":
+                parity["small_workload_run"] = small_fit_parity(args.method)
+    samp_for_cpu = None
+    if large and not args.no_cpu and rank == 0:
+        gi, gp = cpd.cpd_leverage_sample(h, 0, J, args.warmup + args.steps + 2)
+        samp_for_cpu = (gi.cpu().numpy(), (1.0 / (J * gp)).cpu().numpy(),
+                        [cpd.cpd_get_factors(h, k).cpu().numpy() for k in range(N)])
+    h.close()
+    torch.cuda.synchronize()
+
     # end-to-end through the C ABI from pinned host buffers
     e2e = None
+    idx_h = vals_h = None
+    if not args.no_e2e or (large and not args.no_cpu and rank == 0):
+        idx_h = idx.cpu().pin_memory() if not args.no_e2e else idx.cpu()
+        vals_h = vals.cpu().pin_memory() if not args.no_e2e else vals.cpu()
     if not args.no_e2e:
-        idx_h = idx.cpu().pin_memory()
-        vals_h = vals.cpu().pin_memory()
-        init_h = [u.cpu().pin_memory() for u in init]
+        init_h = None if init is None else [u.cpu().pin_memory() for u in init]
+        if large:
+            del idx, vals
+            idx = vals = None
+            torch.cuda.empty_cache()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = cpd.cpd_create(dims, idx_h, vals_h, init_h, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
@@ -462,21 +612,20 @@ def ours(args, world, rank, local):
                 for k in range(N)]
         e2e_s = time.perf_counter() - t0
         h2.close()
-        h2d = idx_h.numel() * 4 + vals_h.numel() * 4 + sum(u.numel() * 4 for u in init_h)
+        h2d = idx_h.numel() * 4 + vals_h.numel() * 4 + (0 if init_h is None else sum(u.numel() * 4 for u in init_h))
         d2h = sum(o.numel() * 4 for o in outs) + 8
         e2e_s = allreduce_max(e2e_s, world)
         e2e = {"value": world * args.steps / e2e_s, "unit": "sweeps/s", "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps, "job": "cpd_create(host COO) + %d sweeps + fit + factors to host"
                % args.steps, "job_seconds": e2e_s, "fit": f2}
+        del outs
 
     cpu = cpu1 = None
-    idx_np = vals_np = None
-    if not args.no_cpu and rank == 0 and w["nnz"] > ORACLE_MAX_NNZ:
-        cpu = {"value": None, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
-               "sample": "not run: the oracle's per-mode layout build of %d nonzeros in host memory exceeds the "
-                         "bounded sample this bench allows" % w["nnz"]}
+    if not args.no_cpu and rank == 0 and large:
+        cpu = run_oracle_large(idx_h, vals_h, samp_for_cpu, w, threads=os.cpu_count() or 1)
     elif not args.no_cpu and rank == 0:
-        idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
+        if idx_np is None:
+            idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
         ncpu = os.cpu_count() or 1
         res = run_oracle(idx_np, vals_np, init_np, w, args.method, list(range(N)), threads=ncpu)
         res1 = run_oracle(idx_np, vals_np, init_np, w, args.method, list(range(N)), threads=1)
@@ -486,15 +635,6 @@ def ours(args, world, rank, local):
                                           "from the initial factors" % (N, ncpu), "seconds": res["seconds"]}
         cpu1 = {"value": (res1["mode_updates"] / N) / res1["seconds"], "unit": "sweeps/s", "cores": 1,
                 "kind": "oracle", "sample": "the same ALS round, 1 thread", "seconds": res1["seconds"]}
-    parity = None
-    if not args.no_parity and rank == 0:
-        if idx_np is None:
-            idx_np, vals_np = idx.cpu().numpy(), vals.cpu().numpy()
-        parity = parity_check(cpd, h, w, args.method, idx_np, vals_np, args.warmup + args.steps + 1,
-                              leaf_rows=args.leaf_rows)
-        if args.workload != "small_uniform_200x150x100":
-            parity["small_workload_run"] = small_fit_parity(args.method)
-    h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -505,6 +645,8 @@ def ours(args, world, rank, local):
                            "leaf_rows": args.leaf_rows or R, "autotuned": tuned,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MB write, outside the events)",
+                           "generate_seconds": gen_s, "generator_draws": draws_used,
+                           "init": "library-drawn N(0,1) from the seed" if init is None else "host N(0,1)",
                            "create_seconds": create_s},
                 "roofline": roofline, "roofline_spmm": roofline_spmm, "cpu_baseline": cpu,
                 "cpu_baseline_1core": cpu1, "parity": parity, "e2e": e2e,
@@ -735,7 +877,7 @@ def batch_reference(args, world, rank, local):
 def main():
     args = parse()
     if args.cpu_worker:
-        cpu_worker(args.cpu_worker)
+        (cpu_worker_large if args.cpu_large else cpu_worker)(args.cpu_worker)
         return
     world, rank, local = dist()
     batched = args.workload in synth.BATCH_WORKLOADS

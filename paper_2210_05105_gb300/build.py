@@ -12,8 +12,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+GENSRC = os.path.join(HERE, "gen")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcpd.so")
+GENLIB = os.path.join(HERE, "libzipfgen.so")   # input generator, separate from the method's library
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -25,8 +27,8 @@ def _nvcc():
     raise RuntimeError("nvcc not found")
 
 
-def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+def sources(d=CSRC):
+    return sorted(os.path.join(d, f) for f in os.listdir(d) if f.endswith(".cu"))
 
 
 def _compile(nvcc, src, extra):
@@ -43,19 +45,22 @@ def build(verbose=False, extra=()):
     nvcc = _nvcc()
     os.makedirs(OBJDIR, exist_ok=True)
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, list(extra)), srcs))
-    objs = [o for o, _ in results]
+    gsrcs = sources(GENSRC)
+    with cf.ThreadPoolExecutor(max_workers=min(12, len(srcs) + len(gsrcs))) as ex:
+        results = list(ex.map(lambda s: _compile(nvcc, s, list(extra)), srcs + gsrcs))
+    objs = [o for o, _ in results[:len(srcs)]]
+    gobjs = [o for o, _ in results[len(srcs):]]
     if verbose:
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    for lib, ob in ((LIB, objs), (GENLIB, gobjs)):
+        tmp = lib + ".tmp"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *ob]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        os.replace(tmp, lib)
     return LIB
 
 

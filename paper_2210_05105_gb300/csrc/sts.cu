@@ -489,7 +489,24 @@ __global__ void __launch_bounds__(STS_NW * 32) sts_walk_df_kernel(StsDfArgs a) {
     const float4* mh4 = reinterpret_cast<const float4*>(Mh);
     const float4* ml4 = reinterpret_cast<const float4*>(Ml);
     float s0h = 0.0f, s0l = 0.0f, s1h = 0.0f, s1l = 0.0f;
-    for (int q = gl; q < npad / 4; q += G) {
+    const int nq = npad / 4;
+    int q = gl;
+    // four vectors of the node per lane in flight: the walk is bound by the
+    // latency of these L2 loads, not by the double-float arithmetic
+    for (; q + 3 * G < nq; q += 4 * G) {
+      float4 th[4], tl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { th[u] = th4[q + u * G]; tl[u] = tl4[q + u * G]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 mh = mh4[q + u * G], ml = ml4[q + u * G];
+        df_dot_step(s0h, s0l, th[u].x, tl[u].x, mh.x, ml.x);
+        df_dot_step(s1h, s1l, th[u].y, tl[u].y, mh.y, ml.y);
+        df_dot_step(s0h, s0l, th[u].z, tl[u].z, mh.z, ml.z);
+        df_dot_step(s1h, s1l, th[u].w, tl[u].w, mh.w, ml.w);
+      }
+    }
+    for (; q < nq; q += G) {
       const float4 th = th4[q], tl = tl4[q], mh = mh4[q], ml = ml4[q];
       df_dot_step(s0h, s0l, th.x, tl.x, mh.x, ml.x);
       df_dot_step(s1h, s1l, th.y, tl.y, mh.y, ml.y);

@@ -126,6 +126,11 @@ WORKLOADS = {
     "zipf_1e5cube_50M": dict(dims=(100_000, 100_000, 100_000), nnz=50_000_000, zipf=1.1,
                              values="lognormal", R=32, J=65536, sweeps=20,
                              data_seed=1002, init_seed=2002, sample_seed=3002),
+    # billion-scale 3-mode workload with Reddit's dims (paper Table 5): Zipf(1.3)
+    # per mode, log(1 + Poisson(3)) values; drawn on the device (libzipfgen)
+    "zipf_reddit_1B": dict(dims=(8_200_000, 177_000, 8_100_000), nnz=1_000_000_000, zipf=1.3,
+                           values="logpoisson", R=100, J=131072, sweeps=20, generator="device",
+                           data_seed=1007, init_seed=2007, sample_seed=3007),
     # 4-mode precision-form workload: values of a planted rank-16 CP model at
     # the drawn coordinates plus Gaussian noise of 10% of their norm (the
     # tensor's zeros are real zeros, so it is not a rank-16 tensor)
@@ -169,6 +174,74 @@ def batch_specs(T, nnz, dims, zipf, values, ranks, J, seed, sweeps):
         out.append(dict(dims=d, nnz=z, zipf=zipf, values=values, R=R, J=j, sweeps=sweeps,
                         data_seed=seed * 1000 + t, init_seed=seed * 1000 + 500 + t, sample_seed=seed * 1000 + 900 + t))
     return out
+
+
+def _genlib():
+    """The device-side generator library (libzipfgen.so, built beside libcpd)."""
+    import ctypes
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libzipfgen.so")
+    if not os.path.exists(path):
+        raise RuntimeError("libzipfgen.so is not built (python -m paper_2210_05105_gb300.build)")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.zg_generate.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P]
+    L.zg_generate.restype = ctypes.c_int
+    L.zg_values_logpoisson.argtypes = [ctypes.c_int64, ctypes.c_uint64, P, ctypes.c_int, P, P]
+    L.zg_values_logpoisson.restype = ctypes.c_int
+    return L
+
+
+def poisson_ge1_cdf(lam=3.0, kmax=64):
+    """Running sums P(X <= x | X >= 1), x = 1..kmax, of Poisson(lam) (last = 1)."""
+    p = np.empty(kmax, dtype=np.float64)
+    term = np.exp(-lam)
+    for x in range(1, kmax + 1):
+        term = term * lam / x
+        p[x - 1] = term
+    c = np.cumsum(p) / (1.0 - np.exp(-lam))
+    c[-1] = 1.0
+    return c
+
+
+def make_tensor_device(dims, nnz, seed, zipf_s, values="logpoisson", device="cuda", max_draws=1 << 40):
+    """Device generator for the billion-scale workload (libzipfgen): draw d
+    picks i_k = perm_k[smallest r with table_k[r] > u_k(d)], u_k(d) from
+    Philox4x64-10 key (seed, 7), counter (d, 0, 0, 0), word k; exactly nnz
+    distinct coordinates with the earliest first draws, in first-draw order;
+    values log(1 + Poisson(3)) with zeros redrawn (Philox key (seed, 8)).
+    The tables are this module's truncated Zipf running sums and the
+    permutations come from numpy's PCG64 with `seed`, as in coo_coordinates.
+    Returns (idx (N, nnz) int32, vals (nnz,) float32, draws used)."""
+    import ctypes
+    import torch
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perms = [torch.from_numpy(rng.permutation(I).astype(np.int32)).to(device) for I in dims]
+    tables = [torch.from_numpy(_zipf_table(I, zipf_s)).to(device) for I in dims]
+    idx = torch.empty((N, nnz), dtype=torch.int32, device=device)
+    L = _genlib()
+    P = ctypes.c_void_p
+    dims_a = (ctypes.c_int64 * N)(*dims)
+    tab_a = (P * N)(*[t.data_ptr() for t in tables])
+    perm_a = (P * N)(*[t.data_ptr() for t in perms])
+    used = ctypes.c_int64(0)
+    stream = P(torch.cuda.current_stream().cuda_stream)
+    rc = L.zg_generate(N, ctypes.cast(dims_a, P), ctypes.cast(tab_a, P), ctypes.cast(perm_a, P), int(seed), int(nnz),
+                       int(max_draws), P(idx.data_ptr()), ctypes.byref(used), stream)
+    if rc != 0:
+        raise RuntimeError("zg_generate failed with code %d" % rc)
+    if values != "logpoisson":
+        raise ValueError(values)
+    cdf = torch.from_numpy(poisson_ge1_cdf(3.0)).to(device)
+    vals = torch.empty(nnz, dtype=torch.float32, device=device)
+    rc = L.zg_values_logpoisson(int(nnz), int(seed), P(cdf.data_ptr()), int(cdf.numel()), P(vals.data_ptr()), stream)
+    if rc != 0:
+        raise RuntimeError("zg_values_logpoisson failed with code %d" % rc)
+    torch.cuda.synchronize()
+    del perms, tables, cdf
+    return idx, vals, int(used.value)
 
 
 def make_tensor_torch(dims, nnz, seed, zipf_s=0.0, values="uniform", device="cuda"):
