@@ -72,7 +72,10 @@ typedef struct {
   uint64_t seed;           /* Philox4x64-10 key word 0 for all draws */
   int32_t leaf_rows;       /* STS-CP rows per tree leaf F; 0 means F = R */
   int32_t input_on_host;   /* 1: idx, vals, init_factors of cpd_create are host memory */
-  int64_t reserved_i64[4];
+  int64_t nnz_sel_capacity; /* deterministic mode only: most selected nonzeros one
+                              downsampled MTTKRP may gather (its sorted work list is
+                              sized from it); 0 = nnz.  More latches CPD_ERR_CAPACITY */
+  int64_t reserved_i64[3];
   int32_t sketched_gram;   /* 0: solve with G = *_{k!=n} U_k^T U_k (Eq. 5, Sec. 4);
                               1: with the Gram of the sampled rows, sum_j w_j h_j h_j^T,
                               i.e. the normal equations of the downsampled problem
@@ -90,7 +93,15 @@ typedef struct {
   int32_t duplicate_policy; /* repeated COO coordinates: 0 = rejected with
                               CPD_ERR_DUPLICATE; 1 = their values are summed into one
                               nonzero (the handle then holds fewer nonzeros) */
-  int32_t reserved_i32[4];
+  int32_t deterministic;   /* 1: bitwise-repeatable runs.  The downsampled MTTKRP then
+                              adds no floating-point value with an atomic: repeated
+                              draws' weights are summed in draw order, and the
+                              selected nonzeros are sorted by output row (stably,
+                              in layout order) and reduced per row in that fixed
+                              order.  Slower; CP-ARLS-LEV and STS-CP only (exact ALS:
+                              CPD_ERR_INVALID_ARG).  0: atomics, faster, repeatable
+                              to float32 rounding */
+  int32_t reserved_i32[3];
 } cpd_options;
 
 /* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */

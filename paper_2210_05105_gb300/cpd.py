@@ -28,9 +28,10 @@ PHASES = ["pinv", "draw", "probe", "scan", "spmm", "solve", "gram", "sampler", "
 class cpd_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("rank", ctypes.c_int32), ("samples", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("leaf_rows", ctypes.c_int32), ("input_on_host", ctypes.c_int32),
-                ("reserved_i64", ctypes.c_int64 * 4), ("sketched_gram", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("spmm_blocks_per_sm", ctypes.c_int32),
-                ("duplicate_policy", ctypes.c_int32), ("reserved_i32", ctypes.c_int32 * 4)]
+                ("nnz_sel_capacity", ctypes.c_int64), ("reserved_i64", ctypes.c_int64 * 3),
+                ("sketched_gram", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("spmm_blocks_per_sm", ctypes.c_int32), ("duplicate_policy", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("reserved_i32", ctypes.c_int32 * 3)]
 
 
 class CpdError(RuntimeError):
@@ -115,7 +116,8 @@ class Handle:
 
 
 def cpd_create(dims, idx, vals, init_factors, method="arls", rank=8, samples=2000, seed=0, leaf_rows=0,
-               stream=None, sketched_gram=False, fast=False, spmm_blocks_per_sm=0, sum_duplicates=False):
+               stream=None, sketched_gram=False, fast=False, spmm_blocks_per_sm=0, sum_duplicates=False,
+               deterministic=False, nnz_sel_capacity=0):
     """Build a handle.  idx (N, nnz) int32, vals (nnz,) float32 and the init
     factors (list of (I_k, R) float32) must all be on the same device: all
     CUDA, or all CPU (then they are copied by the library, host input).
@@ -143,6 +145,8 @@ def cpd_create(dims, idx, vals, init_factors, method="arls", rank=8, samples=200
     opt.precision = 1 if fast else 0
     opt.spmm_blocks_per_sm = int(spmm_blocks_per_sm)
     opt.duplicate_policy = 1 if sum_duplicates else 0
+    opt.deterministic = 1 if deterministic else 0
+    opt.nnz_sel_capacity = int(nnz_sel_capacity)
     dims_arr = (ctypes.c_int64 * N)(*dims)
     if stream is None and torch.cuda.is_available():
         stream = torch.cuda.current_stream()

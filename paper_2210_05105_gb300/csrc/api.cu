@@ -247,6 +247,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
     }
   }
   if (h->opt.method == CPD_STS_CP && (s = cpd_sts_alloc(h)) != CPD_OK) return s;
+  if (h->opt.deterministic && (s = cpd_det_alloc(h)) != CPD_OK) return s;
   if ((s = cpd_dense_init(h)) != CPD_OK) return s;
   if ((s = cpd_sample_init(h)) != CPD_OK) return s;
 
@@ -316,6 +317,9 @@ cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz, const int32_t
     if (b != 0 && b != 1 && b != 2 && b != 4 && b != 8) return CPD_ERR_INVALID_ARG;
   }
   if (opt->duplicate_policy != 0 && opt->duplicate_policy != 1) return CPD_ERR_INVALID_ARG;
+  if (opt->deterministic != 0 && opt->deterministic != 1) return CPD_ERR_INVALID_ARG;
+  if (opt->deterministic && opt->method == CPD_EXACT) return CPD_ERR_INVALID_ARG;
+  if (opt->nnz_sel_capacity < 0) return CPD_ERR_INVALID_ARG;
   // every column key (product of the other modes' dims) must stay below 2^64
   for (int k = 0; k < N; ++k)
     if (dims[k] < 1 || dims[k] > 0x7fffffffll) return CPD_ERR_INVALID_ARG;

@@ -127,6 +127,23 @@ struct cpd_ctx {
 
   std::vector<void*> allocs;
 
+  // deterministic downsampled MTTKRP (options.deterministic): sorted work
+  // lists instead of floating-point atomics
+  int64_t sel_cap = 0;                 // selected nonzeros a call may gather
+  uint32_t* dslot = nullptr;           // Jcap: dedup slot of each draw (EMPTY: none)
+  uint32_t* uq_len = nullptr;          // Jcap: nonzeros of each distinct column
+  unsigned long long* dkeys = nullptr; // max(Jcap, sel_cap) sort keys, and the same again as scratch
+  unsigned long long* dkeys2 = nullptr;
+  uint32_t* dvals = nullptr;           // payloads, and scratch
+  uint32_t* dvals2 = nullptr;
+  uint32_t* dcounts = nullptr;         // radix-sort digit counts for max(Jcap, sel_cap)
+  uint32_t* dlen = nullptr;            // Jcap + 1: column lengths in canonical order, then offsets
+  uint32_t* dwords = nullptr;          // device counts: [0] selected nonzeros kept, [1] scan total
+  uint32_t* sel_e = nullptr;           // sel_cap: layout entry of each canonical position
+  uint32_t* sel_u = nullptr;           // sel_cap: distinct column of each canonical position
+  float* dpart = nullptr;              // ceil(sel_cap / 256) x 2 x Rp run partial sums
+  uint32_t* dflags = nullptr;          // ceil(sel_cap / 256) chunk flags
+
   // launch shapes chosen by cpd_autotune
   int tune_spmm_bps = 2;    // SpMM blocks per SM (1024 threads each up to 2, then 2048 / bps)
   int hot_cap = 0;          // hot-row slots per mode kept by the layout
@@ -355,3 +372,9 @@ cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y);
 cpd_status cpd_scan_u32(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);
 cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t n, int bits,
                               unsigned long long* keys_tmp, uint32_t* vals_tmp);
+cpd_status cpd_radix_sort_u64_dev(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t cap,
+                                  const uint32_t* n_dev, int bits, unsigned long long* keys_tmp, uint32_t* vals_tmp,
+                                  uint32_t* counts, unsigned long long** out_k, uint32_t** out_v);
+// det.cu (options.deterministic)
+cpd_status cpd_det_alloc(cpd_ctx* h);
+cpd_status cpd_det_mttkrp(cpd_ctx* h, int mode, const double* w, int64_t J, float* Y, int64_t* out_nnz_sel);

@@ -716,6 +716,107 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
   }
 }
 
+// ---- solve for 32 < R <= 128: register-tiled Y (P_hi + P_lo) --------------
+// A block of 256 threads (16 x 16) computes tiles of ST_TM = 128 rows x NB
+// columns (NB = 64 or 128 >= Rp): thread (ty, tx) owns rows 8 ty .. 8 ty + 7
+// and columns TC tx .. TC tx + TC - 1 (TC = NB / 16), 8 TC accumulators in
+// registers.  G^+ (hi and lo, R x NB, zero past R) stays in shared memory for
+// the whole grid-stride loop; each 128-row tile of Y is staged transposed
+// (K x 128, consecutive lanes loading consecutive rows, so the transposing
+// stores do not conflict).  Per k the thread reads 8 values of Y and TC of
+// each half of G^+ as 16-byte vectors and issues 16 TC FMAs.  Every output
+// adds its terms in the order of solve_kernel:
+// o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
+constexpr int ST_TM = 128;
+constexpr int ST_YS = ST_TM + 4;   // row stride of the transposed Y tile
+template <int NB>
+__global__ void __launch_bounds__(DTHREADS, 1) solve_tile_kernel(
+    const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R, int Rp,
+    double* __restrict__ colpart) {
+  constexpr int TC = NB / 16;
+  extern __shared__ float4 sm4[];
+  float* Ph = reinterpret_cast<float*>(sm4);     // R x NB
+  float* Pl = Ph + R * NB;                       // R x NB
+  float* Ys = Pl + R * NB;                       // Rp x ST_YS (transposed tile; rows >= R hold Y's zero padding)
+  __shared__ float wsq[16][NB];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  for (int e = t; e < R * NB; e += DTHREADS) {
+    const int a = e / NB, c = e % NB;
+    Ph[e] = c < R ? P2[a * R + c] : 0.0f;
+    Pl[e] = c < R ? P2[R * R + a * R + c] : 0.0f;
+  }
+  float csq[TC];
+#pragma unroll
+  for (int j = 0; j < TC; ++j) csq[j] = 0.0f;
+  const int C4 = Rp / 4;
+  const float4* Y4 = reinterpret_cast<const float4*>(Y);
+  for (int64_t r0 = (int64_t)blockIdx.x * ST_TM; r0 < I; r0 += (int64_t)gridDim.x * ST_TM) {
+    __syncthreads();                             // previous tile consumed (and G^+ staged)
+    // lanes take consecutive rows of one float4 column of the tile
+    for (int e = t; e < ST_TM * C4; e += DTHREADS) {
+      const int row = e % ST_TM, c4 = e / ST_TM;
+      const float4 v = (r0 + row < I) ? Y4[(r0 + row) * C4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      Ys[(4 * c4 + 0) * ST_YS + row] = v.x;
+      Ys[(4 * c4 + 1) * ST_YS + row] = v.y;
+      Ys[(4 * c4 + 2) * ST_YS + row] = v.z;
+      Ys[(4 * c4 + 3) * ST_YS + row] = v.w;
+    }
+    __syncthreads();
+    float acc[8][TC];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < TC; ++j) acc[i][j] = 0.0f;
+#pragma unroll 2
+    for (int a = 0; a < R; ++a) {
+      const float4 y0 = *reinterpret_cast<const float4*>(Ys + a * ST_YS + 8 * ty);
+      const float4 y1 = *reinterpret_cast<const float4*>(Ys + a * ST_YS + 8 * ty + 4);
+      const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+      float ph[TC], pl[TC];
+#pragma unroll
+      for (int v = 0; v < TC / 4; ++v) {
+        const float4 h4 = *reinterpret_cast<const float4*>(Ph + a * NB + TC * tx + 4 * v);
+        const float4 l4 = *reinterpret_cast<const float4*>(Pl + a * NB + TC * tx + 4 * v);
+        ph[4 * v] = h4.x; ph[4 * v + 1] = h4.y; ph[4 * v + 2] = h4.z; ph[4 * v + 3] = h4.w;
+        pl[4 * v] = l4.x; pl[4 * v + 1] = l4.y; pl[4 * v + 2] = l4.z; pl[4 * v + 3] = l4.w;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(yv[i], ph[j], fmaf(yv[i], pl[j], acc[i][j]));
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t row = r0 + 8 * ty + i;
+      if (row < I) {
+#pragma unroll
+        for (int v = 0; v < TC / 4; ++v) {
+          const int c = TC * tx + 4 * v;
+          if (c < Rp)
+            *reinterpret_cast<float4*>(Uw + row * Rp + c) =
+                make_float4(acc[i][4 * v], acc[i][4 * v + 1], acc[i][4 * v + 2], acc[i][4 * v + 3]);
+        }
+#pragma unroll
+        for (int j = 0; j < TC; ++j) csq[j] = fmaf(acc[i][j], acc[i][j], csq[j]);
+      }
+    }
+  }
+  // column sums of squares: per (ty, column) in shared memory, then a fixed-
+  // order sum over ty in float64 per block
+#pragma unroll
+  for (int j = 0; j < TC; ++j) wsq[ty][TC * tx + j] = csq[j];
+  __syncthreads();
+  for (int c = t; c < R; c += DTHREADS) {
+    double s = 0.0;
+    for (int y = 0; y < 16; ++y) s += (double)wsq[y][c];
+    colpart[(int64_t)blockIdx.x * R + c] = s;
+  }
+}
+
+static size_t solve_tile_smem(int R, int NB) {
+  return ((size_t)2 * R * NB + (size_t)cpd_pad4(R) * ST_YS) * sizeof(float);
+}
+
 static int solve_rb(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
 
 // ---- fit ------------------------------------------------------------------
@@ -902,10 +1003,16 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
       solve_lane_kernel<<<nblk, DTHREADS, 0, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     } else if (rb == 16)
       solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
-    else if (rb == 64)
-      solve_kernel<64><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
-    else
-      solve_kernel<128><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
+    else {
+      // one 256-thread block per SM (the tile and G^+ fill most of its shared memory)
+      nblk = (int)std::min<int64_t>(h->num_sms, std::max<int64_t>(cpd_ceil_div(I, ST_TM), 1));
+      if (rb == 64)
+        solve_tile_kernel<64><<<nblk, DTHREADS, solve_tile_smem(R, 64), h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I,
+                                                                                     R, h->Rp, h->colsq);
+      else
+        solve_tile_kernel<128><<<nblk, DTHREADS, solve_tile_smem(R, 128), h->stream>>>(Y, h->Gnpinv_split, h->Uwork,
+                                                                                       I, R, h->Rp, h->colsq);
+    }
     CPD_LAUNCH(h, "solve");
     sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, nblk, R, h->sigma);
     CPD_LAUNCH(h, "sigma");
@@ -945,8 +1052,9 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
       {(const void*)normalize_gram_kernel<1>, s1}, {(const void*)normalize_gram_kernel<3>, s1},
       {(const void*)normalize_gram_kernel<9>, s1}, {(const void*)normalize_gram_kernel<33>, s1},
       {(const void*)pinv_kernel, s2},              {(const void*)solve_kernel<16>, s3},
-      {(const void*)solve_kernel<32>, s3},         {(const void*)solve_kernel<64>, s3},
-      {(const void*)solve_kernel<128>, s3}};
+      {(const void*)solve_kernel<32>, s3},
+      {(const void*)solve_tile_kernel<64>, solve_tile_smem(std::min(R, 64), 64)},
+      {(const void*)solve_tile_kernel<128>, solve_tile_smem(R, 128)}};
   for (const auto& a : attrs) {
     const cpd_status st = cpd_smem_attr(h, a.first, a.second);
     if (st != CPD_OK) return st;

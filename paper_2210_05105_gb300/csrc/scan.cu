@@ -101,9 +101,12 @@ constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 4096 keys per block
 constexpr int RS_WARPS = RS_THREADS / 32;
 
+// n_dev (device, may be NULL): the element count when it is only known on the
+// device (a captured sweep); n is then the capacity the grid was sized for.
 __global__ void radix_hist_kernel(const unsigned long long* __restrict__ keys, int64_t n, int shift,
-                                  uint32_t* __restrict__ counts, int64_t nblk) {
+                                  uint32_t* __restrict__ counts, int64_t nblk, const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t hist[256];
+  if (n_dev) n = min(n, (int64_t)*n_dev);
   hist[threadIdx.x] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -120,8 +123,10 @@ __global__ void radix_hist_kernel(const unsigned long long* __restrict__ keys, i
 // equal digits come from warp match masks, then a prefix over warps.
 __global__ void radix_scatter_kernel(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
                                      unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout,
-                                     int64_t n, int shift, const uint32_t* __restrict__ offs, int64_t nblk) {
+                                     int64_t n, int shift, const uint32_t* __restrict__ offs, int64_t nblk,
+                                     const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t base[256];
+  if (n_dev) n = min(n, (int64_t)*n_dev);
   __shared__ uint32_t wc[RS_WARPS][256];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   base[t] = offs[(int64_t)t * nblk + blockIdx.x];
@@ -193,11 +198,12 @@ cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* va
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
-    radix_hist_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, n, shift, counts, nblk);
+    radix_hist_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, n, shift, counts, nblk, nullptr);
     CPD_LAUNCH(h, "radix_hist");
     cpd_status s = cpd_scan_u32(h, counts, counts, nblk * 256, nullptr);
     if (s != CPD_OK) return s;
-    radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, va, kb, vb, n, shift, counts, nblk);
+    radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, va, kb, vb, n, shift, counts, nblk,
+                                                                       nullptr);
     CPD_LAUNCH(h, "radix_scatter");
     unsigned long long* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
@@ -209,3 +215,34 @@ cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* va
   CPD_CUDA(h, cudaFreeAsync(counts, h->stream));
   return CPD_OK;
 }
+
+// The same sort for a count known only on the device (*n_dev <= cap): grids
+// are sized for cap, blocks past the count exit at once, and the result is
+// left in whichever buffer pair the last pass wrote (*out_k, *out_v), so no
+// copy of cap elements is needed.  counts: 256 * ceil(cap / 4096) words.
+cpd_status cpd_radix_sort_u64_dev(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t cap,
+                                  const uint32_t* n_dev, int bits, unsigned long long* keys_tmp, uint32_t* vals_tmp,
+                                  uint32_t* counts, unsigned long long** out_k, uint32_t** out_v) {
+  unsigned long long *ka = keys, *kb = keys_tmp;
+  uint32_t *va = vals, *vb = vals_tmp;
+  if (cap > 1 && bits > 0) {
+    const int64_t nblk = cpd_ceil_div(cap, RS_TILE);
+    const int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+      const int shift = 8 * p;
+      radix_hist_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, cap, shift, counts, nblk, n_dev);
+      CPD_LAUNCH(h, "radix_hist");
+      cpd_status s = cpd_scan_u32(h, counts, counts, nblk * 256, nullptr);
+      if (s != CPD_OK) return s;
+      radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, va, kb, vb, cap, shift, counts, nblk,
+                                                                         n_dev);
+      CPD_LAUNCH(h, "radix_scatter");
+      unsigned long long* tk = ka; ka = kb; kb = tk;
+      uint32_t* tv = va; va = vb; vb = tv;
+    }
+  }
+  *out_k = ka;
+  *out_v = va;
+  return CPD_OK;
+}
+

@@ -211,7 +211,7 @@ int zg_generate(int N, const int64_t* dims, const double* const* tables, const i
   }
   if (prod >= 18446744073709551615.0L || (long double)nnz > prod) return 1;
   unsigned long long cap = 1024;
-  while ((long double)cap < 2.3L * (long double)nnz) cap <<= 1;
+  while ((long double)cap < 1.6L * (long double)nnz) cap <<= 1;
   const unsigned long long mask = cap - 1;
   unsigned long long *keys = nullptr, *first = nullptr, *distinct = nullptr;
   int* full = nullptr;

@@ -38,15 +38,18 @@ def test_header_functions_are_exported(cpd):
 def test_options_layout_matches_c(tmp_path, cpd):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cpd.h"\nint main(void){'
-                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(cpd_options), offsetof(cpd_options, samples),'
+                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cpd_options), offsetof(cpd_options, samples),'
                    'offsetof(cpd_options, seed), offsetof(cpd_options, leaf_rows),'
-                   'offsetof(cpd_options, input_on_host), offsetof(cpd_options, reserved_i64));return 0;}\n')
+                   'offsetof(cpd_options, input_on_host), offsetof(cpd_options, reserved_i64),'
+                   'offsetof(cpd_options, nnz_sel_capacity), offsetof(cpd_options, deterministic),'
+                   'offsetof(cpd_options, duplicate_policy));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     O = cpd.cpd_options
     assert got == [ctypes.sizeof(O), O.samples.offset, O.seed.offset, O.leaf_rows.offset,
-                   O.input_on_host.offset, O.reserved_i64.offset]
+                   O.input_on_host.offset, O.reserved_i64.offset, O.nnz_sel_capacity.offset,
+                   O.deterministic.offset, O.duplicate_policy.offset]
 
 
 def test_default_options_and_argument_errors(cpd):

@@ -532,3 +532,95 @@ def test_non_finite_gram_reports_singular_gram(cpd):
     assert ei.value.status == 7
     h.close()
 
+
+
+@pytest.mark.parametrize("R", [40, 64, 99, 100, 128])
+def test_tiled_solve_large_rank_matches_oracle(cpd, R):
+    """Solve and renormalisation (Algorithm 1 lines 6-8) at 32 < R <= 128 (the
+    register-tiled kernel: 128-row tiles, ragged at 150 and 1031 rows, R not a
+    multiple of 4 for R = 99) against the oracle's Y G^+ and column norms."""
+    dims = (333, 150, 1031)
+    idx, vals, init = make_case(dims, 20000, R, seed=91)
+    h = create(cpd, dims, idx, vals, init, "arls", R, 1000, seed=9)
+    fs = gpu_factors(cpd, h)
+    rng = np.random.default_rng(R)
+    for mode in (1, 2):
+        Ys = rng.standard_normal((dims[mode], R)).astype(np.float32)
+        sigma = cpd.cpd_gram_solve(h, mode, torch.from_numpy(Ys)).cpu().numpy()
+        G = oc.hadamard_of_grams([oc.gram(U) for U in fs], mode)
+        U_ref, s_ref = oc.solve_and_renorm(Ys.astype(np.float64), oc.pinv_sym(G))
+        assert rel_frob(sigma, s_ref) < 1e-5, mode
+        assert rel_frob(cpd.cpd_get_factors(h, mode).double().cpu().numpy(), U_ref) < 1e-5, mode
+        fs[mode] = cpd.cpd_get_factors(h, mode).double().cpu().numpy()
+    h.close()
+
+
+@pytest.mark.parametrize("method", ["arls", "sts"])
+def test_deterministic_runs_are_bitwise_equal(cpd, method):
+    """options.deterministic: no floating-point atomics in the downsampled
+    MTTKRP, so two runs from the same inputs give bit-identical factors, sigma
+    and fit; the run stays within the method's tolerance of the oracle."""
+    dims, R, J = (300, 200, 150), 16, 3000
+    idx, vals, init = make_case(dims, 40000, R, seed=71, zipf=1.1)
+    runs = []
+    for _ in range(2):
+        h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                           [torch.from_numpy(u).cuda() for u in init], method=method, rank=R, samples=J, seed=5,
+                           deterministic=True)
+        cpd.cpd_als_sweep(h, 3)
+        runs.append(([cpd.cpd_get_factors(h, k).cpu() for k in range(3)], cpd.cpd_get_sigma(h).cpu(), cpd.cpd_fit(h)))
+        h.close()
+    (f1, s1, fit1), (f2, s2, fit2) = runs
+    assert all(torch.equal(a, b) for a, b in zip(f1, f2))
+    assert torch.equal(s1, s2) and fit1 == fit2
+    _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], method, 3, J=J, seed=5)
+    assert abs(fit1 - fits[-1]) < 1e-3
+
+
+def test_deterministic_sampled_mttkrp_matches_oracle(cpd):
+    """The deterministic path of Eq. 7 with caller draws: repeated KRP rows
+    with unequal weights (their weights add), draws that miss every nonzero,
+    and a hot-row (Zipf) tensor; equal to the oracle within 1e-5 and to the
+    atomics path's count of selected nonzeros; repeated calls bitwise equal."""
+    dims, R, J = (400, 300, 200), 12, 5000
+    idx, vals, init = make_case(dims, 60000, R, seed=73, zipf=1.2)
+    hd = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                        [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=5,
+                        deterministic=True)
+    ha = create(cpd, dims, idx, vals, init, "arls", R, J, seed=5)
+    fs = gpu_factors(cpd, hd)
+    rng = np.random.default_rng(74)
+    for mode in range(3):
+        gi, gp = cpd.cpd_leverage_sample(ha, mode, J, 1)
+        si = gi.cpu().numpy().copy()
+        si[:, 100:200] = si[:, 0:100]               # repeated draws
+        w = rng.uniform(0.1, 3.0, J)                # with unequal weights
+        Yd, nd = cpd.cpd_sampled_mttkrp(hd, mode, torch.from_numpy(si), torch.from_numpy(w))
+        Yd2, _ = cpd.cpd_sampled_mttkrp(hd, mode, torch.from_numpy(si), torch.from_numpy(w))
+        Ya, na = cpd.cpd_sampled_mttkrp(ha, mode, torch.from_numpy(si), torch.from_numpy(w))
+        Yo = oc.sampled_mttkrp(idx, vals, dims, fs, mode, si, w)
+        assert rel_frob(Yd.cpu().numpy(), Yo) <= 1e-5, mode
+        assert torch.equal(Yd, Yd2)
+        assert nd == na == oc.selected_nnz(idx, dims, mode, si)
+    hd.close()
+    ha.close()
+
+
+def test_deterministic_capacity_overflow_is_reported(cpd):
+    """nnz_sel_capacity below the selected nonzeros of a call latches
+    CPD_ERR_CAPACITY; the exact method has no deterministic mode."""
+    dims, R, J = (100, 80, 60), 8, 2000
+    idx, vals, init = make_case(dims, 20000, R, seed=75)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=5,
+                       deterministic=True, nnz_sel_capacity=500)
+    gi, gp = cpd.cpd_leverage_sample(h, 0, J, 0)
+    with pytest.raises(cpd.CpdError) as ei:
+        cpd.cpd_sampled_mttkrp(h, 0, gi, 1.0 / (J * gp))
+    assert ei.value.status == 6
+    h.close()
+    with pytest.raises(cpd.CpdError) as ei:
+        cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="exact", rank=R, samples=J, seed=5,
+                       deterministic=True)
+    assert ei.value.status == 1
