@@ -91,11 +91,14 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
   // df64 accumulators (4 chains per entry for ILP) live across all tiles of
   // the block: a block holds ~I / gridDim rows, so the df64 error stays near
   // (rows per block) * 2^-48 of the sum of |terms|; float64 only at the end.
-  float ah[MAXP][4], al[MAXP][4];
+  // (with many entries per thread, R > 72, the entries themselves give the
+  // instruction-level parallelism: one chain each, rows outer, entries inner)
+  constexpr int CH = MAXP > 9 ? 1 : 4;
+  float ah[MAXP][CH], al[MAXP][CH];
 #pragma unroll
   for (int m = 0; m < MAXP; ++m)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) { ah[m][c] = 0.0f; al[m][c] = 0.0f; }
+    for (int c = 0; c < CH; ++c) { ah[m][c] = 0.0f; al[m][c] = 0.0f; }
   const int64_t ntiles = cpd_ceil_div(I, TR);
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t r0 = tl * TR;
@@ -115,6 +118,29 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
       }
     }
     __syncthreads();
+    if constexpr (CH == 1) {
+      for (int q = 0; q < TR / 4; ++q) {
+#pragma unroll
+        for (int m = 0; m < MAXP; ++m) {
+          const int p = t + m * DTHREADS;
+          if (p < npairs) {
+            const float4 x = reinterpret_cast<const float4*>(tile + pa[p] * TRP)[q];
+            const float4 y = reinterpret_cast<const float4*>(tile + pb[p] * TRP)[q];
+            if (fast) {
+              ah[m][0] = fmaf(x.x, y.x, ah[m][0]);
+              ah[m][0] = fmaf(x.y, y.y, ah[m][0]);
+              ah[m][0] = fmaf(x.z, y.z, ah[m][0]);
+              ah[m][0] = fmaf(x.w, y.w, ah[m][0]);
+            } else {
+              df_fma(ah[m][0], al[m][0], x.x, y.x);
+              df_fma(ah[m][0], al[m][0], x.y, y.y);
+              df_fma(ah[m][0], al[m][0], x.z, y.z);
+              df_fma(ah[m][0], al[m][0], x.w, y.w);
+            }
+          }
+        }
+      }
+    } else {
 #pragma unroll
     for (int m = 0; m < MAXP; ++m) {
       int p = t + m * DTHREADS;
@@ -135,12 +161,13 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
           for (int q = 0; q < TR / 4; ++q) {
             const float4 x = ca[q], y = cb[q];
             df_fma(ah[m][0], al[m][0], x.x, y.x);
-            df_fma(ah[m][1], al[m][1], x.y, y.y);
-            df_fma(ah[m][2], al[m][2], x.z, y.z);
-            df_fma(ah[m][3], al[m][3], x.w, y.w);
+            df_fma(ah[m][CH > 1 ? 1 : 0], al[m][CH > 1 ? 1 : 0], x.y, y.y);
+            df_fma(ah[m][CH > 2 ? 2 : 0], al[m][CH > 2 ? 2 : 0], x.z, y.z);
+            df_fma(ah[m][CH > 3 ? 3 : 0], al[m][CH > 3 ? 3 : 0], x.w, y.w);
           }
         }
       }
+    }
     }
     __syncthreads();
   }
@@ -149,9 +176,11 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
   for (int m = 0; m < MAXP; ++m) {
     int p = t + m * DTHREADS;
     if (p < npairs) {
-      df_merge(ah[m][0], al[m][0], ah[m][1], al[m][1]);
-      df_merge(ah[m][2], al[m][2], ah[m][3], al[m][3]);
-      df_merge(ah[m][0], al[m][0], ah[m][2], al[m][2]);
+      if constexpr (CH == 4) {
+        df_merge(ah[m][0], al[m][0], ah[m][CH - 3], al[m][CH - 3]);
+        df_merge(ah[m][CH - 2], al[m][CH - 2], ah[m][CH - 1], al[m][CH - 1]);
+        df_merge(ah[m][0], al[m][0], ah[m][CH - 2], al[m][CH - 2]);
+      }
       out[p] = df_value(ah[m][0], al[m][0]);
     }
   }

@@ -196,8 +196,12 @@ template <int RPT>
 __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
   // hot rows: one float row (stride Rp + 1, so rows start in different banks)
   // per slot, and a touched flag per slot; flushed to Y once per block
-  extern __shared__ float hot_acc[];
-  __shared__ unsigned char order[32][32];   // per warp: chunk positions, shared-memory rows first
+  // dynamic shared memory: per warp 64 bytes of chunk positions (shared-
+  // memory rows first; the cold list starts at the next multiple of E >= the
+  // hot count, so its last index is below 32 + E - 1 <= 63), then the hot rows
+  extern __shared__ float smem_raw[];
+  unsigned char* order = reinterpret_cast<unsigned char*>(smem_raw);
+  float* hot_acc = smem_raw + (blockDim.x >> 5) * 16;
   const int Rp = RPT ? RPT : a.Rp;
   const int S = Rp + 1;
   const int Hs = a.n_hot;
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
   for (int i = threadIdx.x; i < Hs; i += blockDim.x) touched[i] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  unsigned char* ord = order[threadIdx.x >> 5];
+  unsigned char* ord = order + (threadIdx.x >> 5) * 64;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long pk = *reinterpret_cast<const unsigned long long*>(a.counters);
@@ -415,11 +419,16 @@ __global__ void sketch_rows_kernel(MArgs a, const int32_t* __restrict__ idx, con
 // its blocks and holds as many hot rows (Rp + 1 floats and a flag) as fit.
 int cpd_spmm_threads(int bps) { return bps <= 2 ? 1024 : 2048 / bps; }
 int cpd_spmm_hot_slots(int Rp, int bps) {
-  const size_t budget = (size_t)(220 * 1024) / (size_t)std::max(bps, 1);
+  // 227 KB per SM less the 4 KB of per-warp position lists (64 warps)
+  const size_t budget = (size_t)(216 * 1024) / (size_t)std::max(bps, 1);
   return (int)(budget / ((size_t)(Rp + 1) * 4 + 4));
 }
+// dynamic shared memory of the sampled SpMM: position lists, then hot rows
+static size_t spmm_smem(int threads, int n_hot, int Rp) {
+  return (size_t)(threads / 32) * 64 + (size_t)n_hot * ((size_t)(Rp + 1) * 4 + 4);
+}
 cpd_status cpd_spmm_init(cpd_ctx* h) {
-  const size_t shm = (size_t)cpd_spmm_hot_slots(h->Rp, 1) * ((size_t)(h->Rp + 1) * 4 + 4);
+  const size_t shm = spmm_smem(cpd_spmm_threads(1), cpd_spmm_hot_slots(h->Rp, 1), h->Rp);
   for (const void* f : {(const void*)spmm_kernel<0>, (const void*)spmm_kernel<16>, (const void*)spmm_kernel<32>,
                         (const void*)spmm_kernel<64>, (const void*)spmm_kernel<128>}) {
     const cpd_status s = cpd_smem_attr(h, f, shm);
@@ -492,7 +501,7 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
     const int bps = h->tune_spmm_bps;
     a.n_hot = std::min(h->mode[mode].n_hot, cpd_spmm_hot_slots(h->Rp, bps));
     a.hot_rows = h->mode[mode].hot_rows;
-    const size_t shm = (size_t)a.n_hot * ((size_t)(h->Rp + 1) * 4 + 4);
+    const size_t shm = spmm_smem(cpd_spmm_threads(bps), a.n_hot, h->Rp);
     const dim3 grid(h->num_sms * bps), block(cpd_spmm_threads(bps));
     switch (h->Rp) {
       case 16: spmm_kernel<16><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
