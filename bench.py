@@ -1,9 +1,12 @@
 """Benchmark: randomized CP-ALS sweeps per second on one GB300 (or N replicas).
 
-Workload (default): 3-mode tensor 100,000^3 with 50M distinct nonzeros, mode
-indices Zipf(s = 1.1), values lognormal(0, 1), R = 32, J = 65,536,
-CP-ARLS-LEV (or STS-CP with --method sts), float32 factors with float64
-Grams, leverage scores and R x R algebra.  Data is synthetic and seeded.
+Workload (default, the largest single-GPU configuration): 3-mode tensor
+8,200,000 x 177,000 x 8,100,000 (the Reddit tensor's dims) with 1e9 distinct
+nonzeros, mode indices Zipf(s = 1.3), values log(1 + Poisson(3)), R = 100,
+J = 2^17, CP-ARLS-LEV (or STS-CP with --method sts), float32 factors with
+float64-accurate Grams, leverage scores and R x R algebra; the coordinates are
+drawn on the device.  --workload zipf_1e5cube_50M runs the 1e5^3, 5e7-nonzero
+Zipf(1.1), R = 32, J = 65,536 workload.  Data is synthetic and seeded.
 
 A step is one ALS round (Algorithm 1: every mode sampled, MTTKRP'd, solved),
 replayed from a captured CUDA graph with inputs resident in HBM.  Between
@@ -38,7 +41,12 @@ from paper_2210_05105_gb300 import synth
 METRIC = "ALS sweeps/s"
 ORACLE_MAX_NNZ = 60_000_000
 FALLBACK_HBM = 6800.0
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 FP64 FMA / clock / SM at 2070 MHz
+# float32 lane operations per second (an FMA counts as one): 152 SMs x 128
+# FP32 lanes x 2070 MHz; the bound of the df64 and float32 dense kernels
+FP32_LANE_TOPS = 152 * 128 * 2.07e9 / 1e12
+# float32 operations of one double-float multiply-add term (exact TwoProduct
+# 2, TwoSum 6, low-word corrections 2): the Gram and leverage-score terms
+DF64_TERM_OPS = 10
 
 
 def parse():
@@ -53,7 +61,7 @@ def parse():
     p.add_argument("--samples", type=int, default=0, help="override J of the workload")
     p.add_argument("--study-J", default="", help="comma-separated J values: print one line per J (runtime breakdown "
                    "and fit after --steps sweeps), the sample-count study of the paper's Figs. 11-12")
-    p.add_argument("--workload", default="zipf_1e5cube_50M",
+    p.add_argument("--workload", default="zipf_reddit_1B",
                    choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
     p.add_argument("--branches", type=int, default=16, help="concurrent branches of the batched graph")
     p.add_argument("--leaf-rows", type=int, default=0, help="STS-CP rows per tree leaf F (0: F = R)")
@@ -289,14 +297,28 @@ def cpu_worker_large(path):
     dims, R, nnz = meta["dims"], meta["R"], meta["nnz"]
     N = len(dims)
     idx, vals = d["idx"], d["vals"]
-    factors = [np.load(path + ".f%d.npy" % k, mmap_mode="r") if k != 0 else np.zeros((1, R)) for k in range(N)]
-    factors = [np.asarray(f, dtype=np.float64) for f in factors]
-    t0 = time.perf_counter()
-    oc.sampled_mttkrp(idx, vals, dims, factors, 0, d["samp_idx"], d["w"])
-    t_mttkrp = time.perf_counter() - t0
-    big = int(np.argmax(dims))
     m = int(meta["rows"])
-    U = np.asarray(np.load(path + ".f%d.npy" % big, mmap_mode="r")[:m], dtype=np.float64)
+    if "samp_idx" in d:
+        # the GPU's draws and factors
+        factors = [np.load(path + ".f%d.npy" % k) if k != 0 else np.zeros((1, R)) for k in range(N)]
+        factors = [np.asarray(f, dtype=np.float64) for f in factors]
+        samp_idx, wts, t_draw = d["samp_idx"], d["w"], 0.0
+        U = np.asarray(np.load(path + ".big.npy"), dtype=np.float64)
+    else:
+        # the oracle's own samplers and draws over the first m rows of each
+        # factor (N(0, 1) rows), a bounded stand-in for full-height factors
+        rng = np.random.default_rng(int(meta["seed"]))
+        factors = [rng.standard_normal((min(m, dims[k]), R)) for k in range(N)]
+        samplers = [oc.arls_build(U) for U in factors]
+        t0 = time.perf_counter()
+        samp_idx, p, _ = oc.arls_draw(samplers, 0, int(meta["J"]), int(meta["seed"]), 0)
+        t_draw = time.perf_counter() - t0
+        wts = oc.sample_weights(p, int(meta["J"]))
+        U = factors[int(np.argmax(dims))]
+    t0 = time.perf_counter()
+    oc.sampled_mttkrp(idx, vals, dims, factors, 0, samp_idx, wts)
+    t_mttkrp = time.perf_counter() - t0
+    m = U.shape[0]
     t0 = time.perf_counter()
     st = oc.arls_build(U)
     t_build = time.perf_counter() - t0
@@ -304,21 +326,29 @@ def cpu_worker_large(path):
     oc.solve_and_renorm(U, st["Gpinv"])
     t_solve = time.perf_counter() - t0
     S = idx.shape[1]
-    round_s = N * t_mttkrp * (nnz / S) + (t_build + t_solve) * (sum(dims) / m)
+    round_s = N * (t_mttkrp * (nnz / S) + t_draw) + (t_build + t_solve) * (sum(dims) / m)
     print(json.dumps({"seconds": round_s, "t_mttkrp_sample": t_mttkrp, "nnz_sample": S, "t_build": t_build,
-                      "t_solve": t_solve, "rows_sample": m}))
+                      "t_solve": t_solve, "t_draw": t_draw, "rows_sample": m}))
 
 
 def run_oracle_large(idx_h, vals_h, samp, w, threads, S=20_000_000, rows=400_000):
-    samp_idx, wts, fs = samp
+    """samp = (GPU draws, weights, GPU factors), or None: the oracle draws from
+    its own samplers on the first `rows` rows of N(0, 1) factors."""
     dims = w["dims"]
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "case.npz")
-        meta = {"dims": list(dims), "R": w["R"], "nnz": w["nnz"], "rows": rows}
-        np.savez(path, idx=idx_h[:, :S].numpy(), vals=vals_h[:S].numpy(), samp_idx=samp_idx, w=wts,
-                 meta=json.dumps(meta))
-        for k, f in enumerate(fs):
-            np.save(path + ".f%d.npy" % k, f)
+        meta = {"dims": list(dims), "R": w["R"], "nnz": w["nnz"], "rows": rows, "J": w["J"],
+                "seed": w["sample_seed"]}
+        if samp is not None:
+            samp_idx, wts, fs = samp
+            np.savez(path, idx=idx_h[:, :S].numpy(), vals=vals_h[:S].numpy(), samp_idx=samp_idx, w=wts,
+                     meta=json.dumps(meta))
+            for k, f in enumerate(fs):
+                if k != 0:
+                    np.save(path + ".f%d.npy" % k, f)       # factors read by mode 0's MTTKRP
+            np.save(path + ".big.npy", fs[int(np.argmax(dims))][:rows])
+        else:
+            np.savez(path, idx=idx_h[:, :S].numpy(), vals=vals_h[:S].numpy(), meta=json.dumps(meta))
         env = dict(os.environ)
         for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             env[v] = str(threads)
@@ -328,12 +358,15 @@ def run_oracle_large(idx_h, vals_h, samp, w, threads, S=20_000_000, rows=400_000
         if r.returncode != 0:
             raise RuntimeError(r.stderr[-2000:])
         res = json.loads(r.stdout.strip().splitlines()[-1])
+    draws = ("the GPU's %d draws" % w["J"]) if samp is not None else \
+        ("%d draws of its own samplers over the first %d rows of each factor (%.2f s each)" % (w["J"], rows,
+                                                                                             res["t_draw"]))
     return {"value": 1.0 / res["seconds"], "unit": "sweeps/s", "cores": threads, "kind": "oracle",
             "extrapolated": True, "seconds": res["seconds"],
             "sample": "extrapolated ALS round: the oracle's downsampled MTTKRP of mode 0 on the first %d nonzeros "
-                      "with the GPU's %d draws (%.2f s, x nnz / %d x %d modes) plus its CP-ARLS-LEV sampler build and "
+                      "with %s (%.2f s, x nnz / %d x %d modes) plus its CP-ARLS-LEV sampler build and "
                       "solve on %d rows of the largest factor (x all rows); FP64 numpy, %d BLAS threads"
-                      % (S, w["J"], res["t_mttkrp_sample"], S, len(dims), rows, threads)}
+                      % (S, draws, res["t_mttkrp_sample"], S, len(dims), rows, threads)}
 
 
 def small_fit_parity(method):
@@ -386,11 +419,12 @@ def algorithmic(phase, w, stats):
     if phase == "probe":
         return "hbm", J * (N - 1) * 4 + J * 8 + stats["J_u"] * ((N - 1) * R * 4 + R * 4) + J * 16
     if phase in ("sampler", "gram"):
-        I = stats["I_mean"]
-        return "alu", I * R * (R + 1) / 2 * 2   # FP64 flops of the quadratic forms / Gram pairs
+        # df64 terms of the quadratic forms (leverage scores) or Gram pairs,
+        # R(R+1)/2 per row, as float32 lane operations
+        return "alu", stats["I_mean"] * R * (R + 1) / 2 * DF64_TERM_OPS
     if phase == "solve":
-        I = stats["I_mean"]
-        return "hbm", I * Rp * 4 * 2
+        # Y (G+_hi + G+_lo): 2 R^2 FMAs a row
+        return "alu", stats["I_mean"] * 2 * R * R
     if phase == "exact":
         # every nonzero: N indices + value, N - 1 factor rows, one output row update
         nnz = w["nnz"]
@@ -559,16 +593,20 @@ def ours(args, world, rank, local):
         bound, amount = algorithmic(phase, w, stats)
         if bound == "alu":
             ach = amount / (per_launch_ms / 1e3) / 1e12
-            return {"phase": phase, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": "derived FP64 FMA rate"}
+            return {"phase": phase, "bound": "alu", "achieved": ach, "peak": FP32_LANE_TOPS,
+                    "unit": "Tops/s (float32 lane operations)", "frac": ach / FP32_LANE_TOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz", "ms_per_launch": per_launch_ms}
         ach = amount / (per_launch_ms / 1e3) / 1e9
+        t = None if (args.fast or args.sketched) else TRAFFIC_BYTES.get((args.workload, args.method, phase))
         return {"phase": phase, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind}
+                "frac": ach / hbm_peak, "traffic": t, "peak_source": peak_kind, "ms_per_launch": per_launch_ms}
 
-    roofline = roof("exact" if args.method == "exact" else "spmm")
-    if not args.fast and not args.sketched:
-        roofline["traffic"] = TRAFFIC_BYTES.get((args.workload, args.method, roofline["phase"]))
-    roofline_spmm = roofline
+    modelled = [k for k in ("spmm", "exact", "sampler", "gram", "solve") if phases.get(k, (0, 0))[1] > 0]
+    roofline_phases = {k: roof(k) for k in modelled}
+    # the roofline of the line is the kernel class with the most device time
+    top = max(modelled, key=lambda k: phases[k][0])
+    roofline = roofline_phases[top]
+    roofline_spmm = roofline_phases.get("exact" if args.method == "exact" else "spmm")
 
     # parity against the FP64 oracle from the GPU's model after the timed sweeps
     parity = None
@@ -648,7 +686,8 @@ def ours(args, world, rank, local):
                            "generate_seconds": gen_s, "generator_draws": draws_used,
                            "init": "library-drawn N(0,1) from the seed" if init is None else "host N(0,1)",
                            "create_seconds": create_s},
-                "roofline": roofline, "roofline_spmm": roofline_spmm, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_spmm": roofline_spmm, "roofline_phases": roofline_phases,
+                "cpu_baseline": cpu,
                 "cpu_baseline_1core": cpu1, "parity": parity, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "phases_ms_per_sweep": {k: round(v[0], 4) for k, v in phases.items() if v[1]},
@@ -831,6 +870,30 @@ def reference(args, world, rank, local):
     w = synth.WORKLOADS[args.workload]
     dims = w["dims"]
     N = len(dims)
+    if w.get("generator") == "device":
+        # billion-scale: each step one bounded, extrapolated ALS round of the
+        # oracle (the whole tensor does not fit the oracle's per-nonzero arrays)
+        idx_d, vals_d, _ = synth.make_tensor_device(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"])
+        S = 5_000_000
+        idx_h, vals_h = idx_d[:, :S].cpu(), vals_d[:S].cpu()
+        del idx_d, vals_d
+        torch.cuda.empty_cache()
+        ncpu = os.cpu_count() or 1
+        for _ in range(args.warmup):
+            run_oracle_large(idx_h, vals_h, None, w, ncpu, S=S, rows=100_000)
+        res = [run_oracle_large(idx_h, vals_h, None, w, ncpu, S=S, rows=100_000) for _ in range(args.steps)]
+        sec = float(np.mean([r["seconds"] for r in res]))
+        value = 1.0 / sec
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "dims": list(dims), "nnz": w["nnz"], "R": w["R"], "J": w["J"],
+                           "method": args.method, "step": "one extrapolated ALS round of the FP64 oracle"},
+                "cpu_baseline": {"kind": "oracle", "cores": ncpu, "value": value, "extrapolated": True,
+                                 "sample": res[-1]["sample"]},
+                "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
     if torch.cuda.is_available():
         idx, vals = synth.make_tensor_torch(dims, w["nnz"], w["data_seed"], w["zipf"], w["values"], device="cuda")
         idx, vals = idx.cpu().numpy(), vals.cpu().numpy()

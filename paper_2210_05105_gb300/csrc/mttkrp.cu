@@ -158,33 +158,31 @@ __global__ void probe_kernel(MArgs a, const int32_t* __restrict__ idx, const dou
   }
 }
 
-// One step of a lane group on a selected position whose row is held in
-// shared memory (hot slot < Hs): sj * h_uj added to the slot's accumulator.
-// The lane group's KRP row hv stays in registers while the drawn column does
-// not change.
-__device__ __forceinline__ void spmm_hot_step(const MArgs& a, int Rp, int C, int q, int Hs, float* __restrict__ hot_acc,
-                                              uint32_t slot, float sj, uint32_t uj, uint32_t& cu, float4& hv) {
+// One step of a lane group: selected position jj of the chunk (row code r,
+// weight sj, distinct column uj, all shuffled from lane jj) adds sj * h_uj
+// into its output row.  The lane group's KRP row hv stays in registers while
+// the drawn column does not change.
+__device__ __forceinline__ void spmm_step(const MArgs& a, int Rp, int C, int q, int Hs, float* __restrict__ hot_acc,
+                                          float* __restrict__ Y, uint32_t r, float sj, uint32_t uj, uint32_t& cu,
+                                          float4& hv) {
   if (uj != cu) {
     hv = reinterpret_cast<const float4*>(a.H)[(int64_t)uj * C + q];
     cu = uj;
   }
-  float* acc = hot_acc + (size_t)slot * (Rp + 1) + 4 * q;
-  atomicAdd(acc + 0, sj * hv.x);
-  atomicAdd(acc + 1, sj * hv.y);
-  atomicAdd(acc + 2, sj * hv.z);
-  atomicAdd(acc + 3, sj * hv.w);
-  if (q == 0) reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * (Rp + 1))[slot] = 1u;
-}
-
-// The same for a row accumulated in global memory: one 16-byte vector
-// reduction per lane into Y.
-__device__ __forceinline__ void spmm_cold_step(const MArgs& a, int Rp, int C, int q, float* __restrict__ Y, uint32_t row,
-                                               float sj, uint32_t uj, uint32_t& cu, float4& hv) {
-  if (uj != cu) {
-    hv = reinterpret_cast<const float4*>(a.H)[(int64_t)uj * C + q];
-    cu = uj;
+  if (r & CPD_HOT_BIT) {
+    const uint32_t slot = r & ~CPD_HOT_BIT;
+    if ((int)slot < Hs) {
+      float* acc = hot_acc + (size_t)slot * (Rp + 1) + 4 * q;
+      atomicAdd(acc + 0, sj * hv.x);
+      atomicAdd(acc + 1, sj * hv.y);
+      atomicAdd(acc + 2, sj * hv.z);
+      atomicAdd(acc + 3, sj * hv.w);
+      reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * (Rp + 1))[slot] = 1u;
+      return;
+    }
+    r = (uint32_t)a.hot_rows[slot];
   }
-  float* yp = Y + (int64_t)row * Rp + 4 * q;
+  float* yp = Y + (int64_t)r * Rp + 4 * q;
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(sj * hv.x), "f"(sj * hv.y),
                "f"(sj * hv.z), "f"(sj * hv.w)
                : "memory");
@@ -196,12 +194,7 @@ template <int RPT>
 __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
   // hot rows: one float row (stride Rp + 1, so rows start in different banks)
   // per slot, and a touched flag per slot; flushed to Y once per block
-  // dynamic shared memory: per warp 64 bytes of chunk positions (shared-
-  // memory rows first; the cold list starts at the next multiple of E >= the
-  // hot count, so its last index is below 32 + E - 1 <= 63), then the hot rows
-  extern __shared__ float smem_raw[];
-  unsigned char* order = reinterpret_cast<unsigned char*>(smem_raw);
-  float* hot_acc = smem_raw + (blockDim.x >> 5) * 16;
+  extern __shared__ float hot_acc[];
   const int Rp = RPT ? RPT : a.Rp;
   const int S = Rp + 1;
   const int Hs = a.n_hot;
@@ -210,7 +203,6 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
   for (int i = threadIdx.x; i < Hs; i += blockDim.x) touched[i] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  unsigned char* ord = order + (threadIdx.x >> 5) * 64;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long pk = *reinterpret_cast<const unsigned long long*>(a.counters);
@@ -222,7 +214,6 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
   const int E = C >= 32 ? 1 : 32 / C;     // nonzeros per warp instruction
   const int sub = C >= 32 ? 0 : lane / C; // which of the E nonzeros this lane serves
   const int q = C >= 32 ? lane : lane % C;
-  const unsigned lt = (1u << lane) - 1u;
   for (int64_t c = warp; c < nchunks; c += nwarps) {
     const int64_t p = c * 32 + lane;
     // The 32 positions of the chunk meet at most 32 consecutive segments
@@ -241,8 +232,7 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
     const uint32_t segoff = __shfl_sync(CPD_FULL, woff, (int)loc);
     uint32_t row = 0, useg = 0;
     float scale = 0.0f;
-    const bool valid = p < total;
-    if (valid) {
+    if (p < total) {
       useg = seg0 + loc;
       // the entry's address does not wait for the dedup slot: the column's
       // first entry was recorded by the probe
@@ -252,40 +242,37 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
       row = en.x;
       scale = a.dd_w[slot] * __uint_as_float(en.y);
     }
-    // Split the chunk by destination with a ballot: positions whose row is
-    // accumulated in shared memory first, then the others (rows resolved to
-    // their index), each list in steps of E positions, so every step of the
-    // warp takes one path (no hot / cold divergence inside a step).
-    const bool in_smem = valid && (row & CPD_HOT_BIT) && (int)(row & ~CPD_HOT_BIT) < Hs;
-    if (valid && !in_smem && (row & CPD_HOT_BIT)) row = (uint32_t)a.hot_rows[row & ~CPD_HOT_BIT];
-    const unsigned hm = __ballot_sync(CPD_FULL, in_smem);
-    const unsigned cm = __ballot_sync(CPD_FULL, valid && !in_smem);
-    const int nh = __popc(hm), nc = __popc(cm);
-    const int nhp = (nh + E - 1) / E * E;   // cold list starts at a step boundary
-    if (in_smem) ord[__popc(hm & lt)] = (unsigned char)lane;
-    else if (valid) ord[nhp + __popc(cm & lt)] = (unsigned char)lane;
-    __syncwarp();
+    const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
+    // C lanes cover one row of Rp floats (C <= 32 since R <= 128) with
+    // 16-byte vector reductions, so one warp instruction updates E = 32 / C
+    // selected nonzeros at once.  Consecutive positions of a lane group
+    // mostly belong to the same drawn column, so its KRP row is kept in
+    // registers and loaded again only when the column changes.
     uint32_t cu = 0xffffffffu;
     float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int j0 = 0; j0 < nhp; j0 += E) {
-      const int jj = j0 + sub;
-      const bool ok = sub < E && jj < nh;
-      const int src = ok ? ord[jj] : 0;
-      const uint32_t r = __shfl_sync(CPD_FULL, row, src);
-      const float sj = __shfl_sync(CPD_FULL, scale, src);
-      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
-      if (ok) spmm_hot_step(a, Rp, C, q, Hs, hot_acc, r & ~CPD_HOT_BIT, sj, uj, cu, hv);
+    if (RPT && E * C == 32 && cnt == 32) {
+      // a full chunk and a lane-group shape that fills the warp: every step
+      // is valid (four steps unrolled at Rp >= 32, two at Rp = 16: more would
+      // spill at 32 registers)
+#pragma unroll (RPT >= 32 ? 4 : 2)
+      for (int j0 = 0; j0 < 32; j0 += E) {
+        const int jj = j0 + sub;
+        const uint32_t r = __shfl_sync(CPD_FULL, row, jj);
+        const float sj = __shfl_sync(CPD_FULL, scale, jj);
+        const uint32_t uj = __shfl_sync(CPD_FULL, useg, jj);
+        spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
+      }
+    } else {
+      for (int j0 = 0; j0 < cnt; j0 += E) {
+        const int jj = j0 + sub;
+        const int src = jj < 32 ? jj : 31;
+        const uint32_t r = __shfl_sync(CPD_FULL, row, src);
+        const float sj = __shfl_sync(CPD_FULL, scale, src);
+        const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
+        if (!(sub < E && jj < cnt)) continue;
+        spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
+      }
     }
-    for (int j0 = nhp; j0 < nhp + nc; j0 += E) {
-      const int jj = j0 + sub;
-      const bool ok = sub < E && jj < nhp + nc;
-      const int src = ok ? ord[jj] : 0;
-      const uint32_t r = __shfl_sync(CPD_FULL, row, src);
-      const float sj = __shfl_sync(CPD_FULL, scale, src);
-      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
-      if (ok) spmm_cold_step(a, Rp, C, q, Y, r, sj, uj, cu, hv);
-    }
-    __syncwarp();
   }
   // flush the block's hot rows that it touched
   __syncthreads();
@@ -419,13 +406,13 @@ __global__ void sketch_rows_kernel(MArgs a, const int32_t* __restrict__ idx, con
 // its blocks and holds as many hot rows (Rp + 1 floats and a flag) as fit.
 int cpd_spmm_threads(int bps) { return bps <= 2 ? 1024 : 2048 / bps; }
 int cpd_spmm_hot_slots(int Rp, int bps) {
-  // 227 KB per SM less the 4 KB of per-warp position lists (64 warps)
-  const size_t budget = (size_t)(216 * 1024) / (size_t)std::max(bps, 1);
+  const size_t budget = (size_t)(220 * 1024) / (size_t)std::max(bps, 1);
   return (int)(budget / ((size_t)(Rp + 1) * 4 + 4));
 }
-// dynamic shared memory of the sampled SpMM: position lists, then hot rows
+// dynamic shared memory of the sampled SpMM: the hot rows and their flags
 static size_t spmm_smem(int threads, int n_hot, int Rp) {
-  return (size_t)(threads / 32) * 64 + (size_t)n_hot * ((size_t)(Rp + 1) * 4 + 4);
+  (void)threads;
+  return (size_t)n_hot * ((size_t)(Rp + 1) * 4 + 4);
 }
 cpd_status cpd_spmm_init(cpd_ctx* h) {
   const size_t shm = spmm_smem(cpd_spmm_threads(1), cpd_spmm_hot_slots(h->Rp, 1), h->Rp);

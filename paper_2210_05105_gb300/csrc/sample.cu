@@ -24,16 +24,25 @@ constexpr int LEV_THREADS = 256;
 // ~2^-48 relative instead of float64 FMAs at 1/64 rate.  Also writes the sum
 // of each block's scores.  (The tile's row stride 257 keeps the transposing
 // stores free of bank conflicts.)
-__global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restrict__ U, int64_t I, int R, int Rp,
-                                                          const double* __restrict__ X, double* __restrict__ ell,
-                                                          double* __restrict__ blk, int fast) {
+// SPLIT threads share a row (blockDim = SPLIT * LEV_THREADS): thread part h
+// takes rows a = h, h + SPLIT, ... of the triangle, and part 0 merges the
+// partial double-floats in part order (deterministic).  Large R gives each
+// row R(R+1)/2 terms while the transposed tile limits a block per SM, so the
+// split supplies the warps that hide the df64 chains' latency.
+template <int SPLIT>
+__global__ void __launch_bounds__(LEV_THREADS * SPLIT) lev_kernel(const float* __restrict__ U, int64_t I, int R,
+                                                                  int Rp, const double* __restrict__ X,
+                                                                  double* __restrict__ ell, double* __restrict__ blk,
+                                                                  int fast) {
   extern __shared__ float4 lsm4[];
   const int npairs = R * (R + 1) / 2;
   float2* Xs = reinterpret_cast<float2*>(lsm4);                 // npairs (hi, lo), row-major upper triangle
   float* us = reinterpret_cast<float*>(Xs + npairs);            // Rp x 257: column c of row t at c * 257 + t
   __shared__ double red[LEV_THREADS / 32];
-  const int t = threadIdx.x;
-  for (int p = t; p < npairs; p += LEV_THREADS) {
+  __shared__ float2 partial[SPLIT > 1 ? SPLIT - 1 : 1][LEV_THREADS];
+  const int tid = threadIdx.x;
+  const int t = tid % LEV_THREADS, h = tid / LEV_THREADS;
+  for (int p = tid; p < npairs; p += LEV_THREADS * SPLIT) {
     int a = 0, rem = p;
     while (rem >= R - a) { rem -= R - a; ++a; }
     const int b = a + rem;
@@ -42,19 +51,18 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
     Xs[p] = make_float2(hi, (float)(x - (double)hi));
   }
   const int64_t r0 = (int64_t)blockIdx.x * LEV_THREADS;
-  for (int e = t; e < LEV_THREADS * Rp; e += LEV_THREADS) {   // coalesced rows -> transposed tile
+  for (int e = tid; e < LEV_THREADS * Rp; e += LEV_THREADS * SPLIT) {   // coalesced rows -> transposed tile
     const int rr = e / Rp, c = e % Rp;
     us[c * (LEV_THREADS + 1) + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
   }
   __syncthreads();
   const int64_t i = r0 + t;
-  double l = 0.0;
+  float lh = 0.0f, ll = 0.0f;
   if (i < I) {
-    float lh = 0.0f, ll = 0.0f;
-    int p = 0;
     if (fast) {                          // float32 (precision option 1), two chains
       float l2 = 0.0f;
-      for (int a = 0; a < R; ++a) {
+      for (int a = h; a < R; a += SPLIT) {
+        int p = a * R - a * (a - 1) / 2;
         const float ua = us[a * (LEV_THREADS + 1) + t];
         int b = a;
         for (; b + 1 < R; b += 2, p += 2) {
@@ -68,7 +76,8 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
       // two independent df64 chains (even and odd b) for instruction-level
       // parallelism; merged at the end
       float lh2 = 0.0f, ll2 = 0.0f;
-      for (int a = 0; a < R; ++a) {
+      for (int a = h; a < R; a += SPLIT) {
+        int p = a * R - a * (a - 1) / 2;
         const float ua = us[a * (LEV_THREADS + 1) + t];
         int b = a;
         for (; b + 1 < R; b += 2, p += 2) {
@@ -88,18 +97,30 @@ __global__ void __launch_bounds__(LEV_THREADS) lev_kernel(const float* __restric
           const float pl = __fmaf_rn(ua, ub, -ph);
           df_fma(lh, ll, ph, x.x);
           ll = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll));
-          ++p;
         }
       }
       df_merge(lh, ll, lh2, ll2);
     }
+  }
+  if (SPLIT > 1) {
+    if (h > 0) partial[h - 1][t] = make_float2(lh, ll);
+    __syncthreads();
+    if (h == 0)
+      for (int q = 0; q < SPLIT - 1; ++q) {
+        const float2 o = partial[q][t];
+        if (fast) lh += o.x; else df_merge(lh, ll, o.x, o.y);
+      }
+  }
+  if (h > 0) return;
+  double l = 0.0;
+  if (i < I) {
     l = df_value(lh, ll);
     ell[i] = l;
   }
-  // block sum in a fixed order
+  // block sum in a fixed order (the first LEV_THREADS threads)
   double s = warp_sum(l);
   if ((t & 31) == 0) red[t >> 5] = s;
-  __syncthreads();
+  asm volatile("bar.sync 1, %0;" ::"n"(LEV_THREADS));
   if (t == 0) {
     double b = 0.0;
     for (int w = 0; w < LEV_THREADS / 32; ++w) b += red[w];
@@ -238,11 +259,21 @@ size_t lev_smem(int R) {
   return (size_t)npairs * 8 + (size_t)(LEV_THREADS + 1) * cpd_pad4(R) * 4;
 }
 
+int lev_split(int R) { return R > 64 ? 4 : R > 32 ? 2 : 1; }
+
 cpd_status quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
                         double* cdf) {
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
-  lev_kernel<<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
-                                                                       h->opt.precision);
+  const int sp = lev_split(h->R);
+  if (sp == 4)
+    lev_kernel<4><<<(unsigned)nb, LEV_THREADS * 4, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                               h->opt.precision);
+  else if (sp == 2)
+    lev_kernel<2><<<(unsigned)nb, LEV_THREADS * 2, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                               h->opt.precision);
+  else
+    lev_kernel<1><<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                           h->opt.precision);
   CPD_LAUNCH(h, "lev");
   cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(q, I, blk, cdf);
   CPD_LAUNCH(h, "cdf");
@@ -266,7 +297,10 @@ cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double*
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
 // once, outside any stream capture).
 cpd_status cpd_sample_init(cpd_ctx* h) {
-  { const cpd_status st_ = cpd_smem_attr(h, (const void*)lev_kernel, lev_smem(h->R)); if (st_ != CPD_OK) return st_; }
+  for (const void* f : {(const void*)lev_kernel<1>, (const void*)lev_kernel<2>, (const void*)lev_kernel<4>}) {
+    const cpd_status st_ = cpd_smem_attr(h, f, lev_smem(h->R));
+    if (st_ != CPD_OK) return st_;
+  }
   return CPD_OK;
 }
 

@@ -44,8 +44,11 @@ def test_create_normalises_and_grams(cpd):
     h.close()
 
 
-def test_arls_sampler_state_matches_oracle(cpd):
-    h, idx, vals, init, cfg = _small(cpd)
+@pytest.mark.parametrize("R,dims", [(8, (200, 150, 100)), (40, (400, 300, 250)), (100, (600, 500, 450))])
+def test_arls_sampler_state_matches_oracle(cpd, R, dims):
+    """Leverage scores and running sums (Algorithm 2) at R = 8 (one thread a
+    row), 40 (two) and 100 (four threads sharing a row)."""
+    h, idx, vals, init, cfg = _small(cpd, R=R, dims=dims)
     fs = gpu_factors(cpd, h)
     for k in range(3):
         st = oc.arls_build(fs[k])
