@@ -251,8 +251,10 @@ def parity_check_large(cpd, h, w, method, idx, vals, sweep_id, nrows=512):
                    "on %d random output rows" % nrows, "mode": mode, "fit_gpu": cpd.cpd_fit(h), "fit_oracle": None}
     if method == "arls":
         gi, gp = cpd.cpd_leverage_sample(h, mode, J, sweep_id)
-        oi, op, near = oc.arls_draw([oc.arls_build(U) if k != mode else {"C": 1.0, "cdf": np.ones(1), "ell": np.ones(1)}
-                                     for k, U in enumerate(fs)], mode, J, w["sample_seed"], sweep_id)
+        smp = [oc.arls_build(U) if k != mode else None for k, U in enumerate(fs)]
+        oi, op, near = oc.arls_draw(smp, mode, J, w["sample_seed"], sweep_id, tie_tol="conditioned")
+        out["tie_window"] = "max(1e-12, 8 cond(G_k) 2^-53) C_k; cond(G_k) = %s" % (
+            ["%.3g" % oc.gram_condition(x["G"]) for x in smp if x is not None])
         gi_np = gi.cpu().numpy()
         mism = np.any(gi_np != oi, axis=0)
         ok = ~mism

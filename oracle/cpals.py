@@ -209,6 +209,22 @@ def inverse_cdf(cdf, ell, t):
     return np.where(i >= cdf.shape[0], last, i).astype(np.int64)
 
 
+def gram_condition(Gk):
+    """2-norm condition number lambda_max / lambda_min of a symmetric PSD
+    Gram from its eigenvalues (inf when singular)."""
+    lam = np.linalg.eigvalsh(0.5 * (np.asarray(Gk) + np.asarray(Gk).T))
+    return float(lam[-1] / lam[0]) if lam[0] > 0 else float("inf")
+
+
+def arls_tie_tolerance(sampler, floor=1e-12):
+    """Tie window of a CP-ARLS-LEV draw on factor k, relative to C_k: a float64
+    Gram is known to 2^-53 of its entries, so G_k^+ -- and every leverage
+    score and running sum built on it -- is determined only to about
+    cond(G_k) 2^-53 relative, whatever the arithmetic that follows.  The
+    window is max(floor, 8 cond(G_k) 2^-53)."""
+    return max(floor, 8.0 * gram_condition(sampler["G"]) * 2.0 ** -53)
+
+
 def arls_draw(samplers, n, J, seed, sweep, tie_tol=1e-12):
     """Draw J rows of U_{!=n} from the product of per-factor leverage scores.
 
@@ -216,6 +232,7 @@ def arls_draw(samplers, n, J, seed, sweep, tie_tol=1e-12):
     i_k = inverse CDF of dist_k at u * C_k.  Returns (idx (N, J) with row n
     set to -1, p (J,) = prod_k ell_k[i_k] / C_k, near_tie (J,) bool marking
     draws whose target lies within tie_tol * C_k of a bin boundary).
+    tie_tol is a number, or "conditioned" for arls_tie_tolerance(sampler k).
     """
     N = len(samplers)
     idx = np.full((N, J), -1, dtype=np.int64)
@@ -235,7 +252,7 @@ def arls_draw(samplers, n, J, seed, sweep, tie_tol=1e-12):
         p = p * (s["ell"][ik] / s["C"] if s["C"] > 0 else 0.0)
         hi = s["cdf"][ik]
         lo = np.where(ik > 0, s["cdf"][np.maximum(ik - 1, 0)], 0.0)
-        tol = tie_tol * s["C"]
+        tol = (arls_tie_tolerance(s) if tie_tol == "conditioned" else tie_tol) * s["C"]
         near |= (np.abs(hi - t) <= tol) | ((ik > 0) & (np.abs(t - lo) <= tol))
     return idx, p, near
 

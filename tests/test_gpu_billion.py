@@ -4,8 +4,11 @@ nonzeros, log(1 + Poisson(3)) values, R = 100, J = 2^17), in the launch
 configuration the bench times, after one captured ALS round:
 
 * all 131,072 CP-ARLS-LEV draws of a mode update equal the FP64 oracle's
-  inverse-CDF draws from the same factors (ties at 1e-12 C excepted), with
-  probabilities to 1e-10 relative;
+  inverse-CDF draws from the same factors, ties excepted: a draw within
+  max(1e-12, 8 cond(G_k) 2^-53) C_k of a bin boundary (the factor Grams of
+  this Zipf(1.3) tensor grow ill-conditioned, and a float64 Gram fixes G_k^+
+  and the leverage scores only to ~cond(G_k) 2^-53); probabilities agree to
+  64 cond_max^2 2^-53 relative (a quadratic form in G_k^+ can lose cond^2);
 * the downsampled MTTKRP of those draws equals the oracle's on 512 random
   output rows (their nonzeros picked out of the device COO), 1e-5 relative;
 * the solve and renormalisation equal the oracle's on those rows.
@@ -35,13 +38,17 @@ def test_billion_scale_mode_update_matches_oracle():
     fs = [cpd.cpd_get_factors(h, k).double().cpu().numpy() for k in range(3)]
     gi, gp = cpd.cpd_leverage_sample(h, mode, J, sweep)
     samplers = [oc.arls_build(U) if k != mode else None for k, U in enumerate(fs)]
-    oi, op, near = oc.arls_draw(samplers, mode, J, W["sample_seed"], sweep)
+    oi, op, near = oc.arls_draw(samplers, mode, J, W["sample_seed"], sweep, tie_tol="conditioned")
+    conds = [oc.gram_condition(s["G"]) for s in samplers if s is not None]
     gi_np = gi.cpu().numpy()
     mism = np.any(gi_np != oi, axis=0)
-    print("billion-scale ARLS: %d draws, %d near ties, %d differing" % (J, int(near.sum()), int(mism.sum())))
+    print("billion-scale ARLS: %d draws, %d near ties, %d differing; cond(G_k) %s"
+          % (J, int(near.sum()), int(mism.sum()), ["%.2e" % c for c in conds]))
     assert not np.any(mism & ~near)
     ok = ~mism
-    assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-10
+    perr = np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok])
+    print("probability max rel err %.2e" % perr)
+    assert perr < max(1e-10, 64 * max(conds) ** 2 * 2.0 ** -53)
     w = 1.0 / (J * gp)
     Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, gi, w)
     rows = np.sort(np.random.default_rng(5).choice(dims[mode], size=512, replace=False))

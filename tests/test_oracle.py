@@ -435,3 +435,25 @@ def test_sketched_gram_als_solves_consistent_problems_exactly():
     init = synth.init_factors(dims, 3, 42)
     _, fits = oc.als(idx, vals, dims, init, "arls", 60, J=200, seed=5, sketched=True)
     assert fits[-1] > 0.9999
+
+
+def test_arls_tie_window_follows_gram_conditioning():
+    """The conditioning-aware tie window: the leverage scores of a factor
+    computed from two float64 Grams that differ by their last-bit rounding
+    differ by about cond(G) 2^-53 relative, inside max(1e-12, 8 cond 2^-53),
+    and the window reduces to the 1e-12 floor for a well-conditioned factor."""
+    rng = np.random.default_rng(12)
+    good = rng.standard_normal((4000, 6))
+    assert oc.arls_tie_tolerance(oc.arls_build(good)) == 1e-12
+    # columns nearly collinear: cond ~ 1e9
+    base = rng.standard_normal((4000, 1))
+    bad = base + 1e-4 * rng.standard_normal((4000, 6))
+    st = oc.arls_build(bad)
+    cond = oc.gram_condition(st["G"])
+    assert cond > 1e7
+    G2 = st["G"] * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=st["G"].shape))
+    G2 = 0.5 * (G2 + G2.T)
+    ell2 = oc.leverage_scores(bad, oc.pinv_sym(G2))
+    drift = np.max(np.abs(np.cumsum(ell2) - st["cdf"])) / st["C"]
+    assert drift > 1e-12                               # the fixed floor alone would not cover it
+    assert drift <= oc.arls_tie_tolerance(st)
