@@ -186,6 +186,99 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
   }
 }
 
+// Register-blocked Gram for R > 64 (precision 0): thread (rg, bi) owns the
+// 4 x 4 block bi of the Gram's upper block triangle (columns 4 a0 .. + 3 by
+// 4 b0 .. + 3) for the rows of row group rg.  Per row it reads two float4 of
+// the row-major tile and adds 16 exact float32 products into 16 independent
+// double-float chains; every GB_FLUSH tiles the chains are added into
+// float64 accumulators, so each df64 chain spans at most GB_FLUSH * TR / nrg
+// rows (error ~ that many 2^-48 of the sum of |terms|).  Each (block, row
+// group) writes its own float64 partial Gram (gram_reduce_kernel sums them in
+// a fixed order).
+constexpr int GB_FLUSH = 4;
+constexpr int GB_MAXT = 544;   // threads: one row group of nblk <= 528 blocks (16 independent chains each)
+__global__ void __maxnreg__(120) gram_blk_kernel(
+    const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
+    const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int nrg) {
+  extern __shared__ float4 gbs4[];
+  float* tile = reinterpret_cast<float*>(gbs4);           // TR x Rp, row-major
+  __shared__ float inv[CPD_MAX_RANK];
+  __shared__ unsigned char ba[CPD_MAX_RANK / 4 * (CPD_MAX_RANK / 4 + 1) / 2];
+  __shared__ unsigned char bb[CPD_MAX_RANK / 4 * (CPD_MAX_RANK / 4 + 1) / 2];
+  const int t = threadIdx.x;
+  const int nb4 = Rp / 4;
+  const int nblk = nb4 * (nb4 + 1) / 2;
+  for (int r = t; r < R; r += blockDim.x) {
+    double sv = do_scale ? sigma[r] : 0.0;
+    inv[r] = (sv > 0.0) ? (float)(1.0 / sv) : 1.0f;
+  }
+  for (int e = t; e < nblk; e += blockDim.x) {
+    int a = 0, rem = e;
+    while (rem >= nb4 - a) { rem -= nb4 - a; ++a; }
+    ba[e] = (unsigned char)a;
+    bb[e] = (unsigned char)(a + rem);
+  }
+  __syncthreads();
+  const int bi = t % nblk, rg = t / nblk;
+  const bool active = rg < nrg;
+  const int a0 = 4 * ba[bi], b0 = 4 * bb[bi];
+  float ah[4][4], al[4][4];
+  double ad[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { ah[i][j] = 0.0f; al[i][j] = 0.0f; ad[i][j] = 0.0; }
+  const int64_t ntiles = cpd_ceil_div(I, TR);
+  int nt = 0;
+  for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+    const int64_t r0 = tl * TR;
+    __syncthreads();                             // previous tile consumed
+    for (int e = t; e < TR * Rp; e += blockDim.x) {
+      const int rr = e / Rp, c = e % Rp;
+      const int64_t i = r0 + rr;
+      float v = 0.0f;
+      if (i < I) {
+        if (c < R) v = Uin[i * Rp + c] * inv[c];
+        Uout[i * Rp + c] = v;
+      }
+      tile[e] = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 1
+      for (int rr = rg; rr < TR; rr += nrg) {
+        const float4 x = *reinterpret_cast<const float4*>(tile + rr * Rp + a0);
+        const float4 y = *reinterpret_cast<const float4*>(tile + rr * Rp + b0);
+        const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_fma(ah[i][j], al[i][j], xv[i], yv[j]);
+      }
+      if (++nt == GB_FLUSH) {
+        nt = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            ad[i][j] += df_value(ah[i][j], al[i][j]);
+            ah[i][j] = 0.0f;
+            al[i][j] = 0.0f;
+          }
+      }
+    }
+  }
+  if (!active) return;
+  double* out = gpart + ((int64_t)blockIdx.x * nrg + rg) * (R * (R + 1) / 2);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + i, b = b0 + j;
+      if (a <= b && b < R) out[a * R - a * (a - 1) / 2 + (b - a)] = ad[i][j] + df_value(ah[i][j], al[i][j]);
+    }
+}
+
 // G = sum of block partials, one warp per Gram entry: lane l sums the
 // partials l, l+32, ... in order, then a fixed butterfly (deterministic).
 __global__ void gram_reduce_kernel(const double* __restrict__ gpart, int nblk, int R, double* __restrict__ G) {
@@ -936,6 +1029,21 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
   }
   size_t shm = (size_t)TRP * R * sizeof(float);
   const int npairs = R * (R + 1) / 2;
+  if (R > 64 && !h->opt.precision) {
+    // register-blocked kernel: (4x4 blocks of the upper block triangle) x row
+    // groups per CTA, one CTA per SM, one partial per (CTA, row group)
+    const int nb4 = h->Rp / 4, nblk = nb4 * (nb4 + 1) / 2;
+    const int nrg = 1;
+    if (nblk > GB_MAXT) return cpd_fail(h, CPD_ERR_INVALID_ARG, "Gram block triangle exceeds the kernel's block size");
+    const int grid = std::max(1, std::min(h->num_sms, h->gram_blocks / nrg));
+    gram_blk_kernel<<<grid, nblk * nrg, (size_t)TR * h->Rp * sizeof(float), h->stream>>>(Uin, Uout, I, R, h->Rp,
+                                                                                          sigma, do_scale, h->Gpart,
+                                                                                          nrg);
+    CPD_LAUNCH(h, "gram_blk");
+    gram_reduce_kernel<<<std::max(1, (npairs + 7) / 8), 256, 0, h->stream>>>(h->Gpart, grid * nrg, R, G);
+    CPD_LAUNCH(h, "gram_reduce");
+    return CPD_OK;
+  }
   // Gram entries per thread: ceil(npairs / 256) rounded up to 1, 3, 9 or 33
   if (npairs <= DTHREADS)
     normalize_gram_kernel<1><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale,

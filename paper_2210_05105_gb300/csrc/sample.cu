@@ -74,12 +74,35 @@ __global__ void __launch_bounds__(LEV_THREADS * SPLIT) lev_kernel(const float* _
       lh += l2;
     } else {
       // two independent df64 chains (even and odd b) for instruction-level
-      // parallelism; merged at the end
+      // parallelism, four when the row is split (large R: fewer warps); merged
+      // at the end
       float lh2 = 0.0f, ll2 = 0.0f;
       for (int a = h; a < R; a += SPLIT) {
         int p = a * R - a * (a - 1) / 2;
         const float ua = us[a * (LEV_THREADS + 1) + t];
         int b = a;
+        if (SPLIT > 1) {
+          float lh3 = 0.0f, ll3 = 0.0f, lh4 = 0.0f, ll4 = 0.0f;
+          for (; b + 3 < R; b += 4, p += 4) {
+            const float ub0 = us[b * (LEV_THREADS + 1) + t], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t];
+            const float ub2 = us[(b + 2) * (LEV_THREADS + 1) + t], ub3 = us[(b + 3) * (LEV_THREADS + 1) + t];
+            const float2 x0 = Xs[p], x1 = Xs[p + 1], x2 = Xs[p + 2], x3 = Xs[p + 3];
+            const float ph0 = __fmul_rn(ua, ub0), ph1 = __fmul_rn(ua, ub1);
+            const float ph2 = __fmul_rn(ua, ub2), ph3 = __fmul_rn(ua, ub3);
+            const float pl0 = __fmaf_rn(ua, ub0, -ph0), pl1 = __fmaf_rn(ua, ub1, -ph1);
+            const float pl2 = __fmaf_rn(ua, ub2, -ph2), pl3 = __fmaf_rn(ua, ub3, -ph3);
+            df_fma(lh, ll, ph0, x0.x);
+            df_fma(lh2, ll2, ph1, x1.x);
+            df_fma(lh3, ll3, ph2, x2.x);
+            df_fma(lh4, ll4, ph3, x3.x);
+            ll = __fmaf_rn(pl0, x0.x, __fmaf_rn(ph0, x0.y, ll));
+            ll2 = __fmaf_rn(pl1, x1.x, __fmaf_rn(ph1, x1.y, ll2));
+            ll3 = __fmaf_rn(pl2, x2.x, __fmaf_rn(ph2, x2.y, ll3));
+            ll4 = __fmaf_rn(pl3, x3.x, __fmaf_rn(ph3, x3.y, ll4));
+          }
+          df_merge(lh3, ll3, lh4, ll4);
+          df_merge(lh2, ll2, lh3, ll3);
+        }
         for (; b + 1 < R; b += 2, p += 2) {
           const float ub0 = us[b * (LEV_THREADS + 1) + t], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t];
           const float2 x0 = Xs[p], x1 = Xs[p + 1];
