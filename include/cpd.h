@@ -316,6 +316,17 @@ cpd_status cpd_autotune(cpd_handle h, int32_t* out_choices);
  */
 cpd_status cpd_sts_rescans(cpd_handle h, int64_t* out);
 
+/*
+ * Test hook of the bounded waits of the tensor-core Gram (precision 1, R <= 64):
+ * sets their limit to wait_cycles SM clock cycles (0 restores the default,
+ * ~2 s), and with suppress_mma = 1 the kernel issues no MMA, so that every
+ * wait runs out.  The kernel then latches CPD_ERR_TIMEOUT (returned by the
+ * next synchronising call), frees its tensor memory and writes zero partial
+ * Grams; nothing is left in flight.  suppress_mma = 1 needs wait_cycles > 0.
+ * Lets the timeout path be exercised without a device fault.
+ */
+cpd_status cpd_debug_gram_wait(cpd_handle h, int64_t wait_cycles, int32_t suppress_mma);
+
 /* Wait for the handle's stream and return the first latched device error. */
 cpd_status cpd_synchronize(cpd_handle h);
 

@@ -19,7 +19,7 @@ STATUS = {0: "CPD_OK", 1: "CPD_ERR_INVALID_ARG", 2: "CPD_ERR_OUT_OF_RANGE_INDEX"
           8: "CPD_ERR_TIMEOUT", 9: "CPD_ERR_NOT_FINITE"}
 EXPORTS = ["cpd_default_options", "cpd_create", "cpd_leverage_sample", "cpd_sampled_mttkrp", "cpd_exact_mttkrp",
            "cpd_gram_solve", "cpd_als_sweep", "cpd_fit", "cpd_get_factors", "cpd_set_factors", "cpd_get_sigma",
-           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_sampled_mttkrp_noalloc", "cpd_sts_rescans", "cpd_synchronize",
+           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_sampled_mttkrp_noalloc", "cpd_sts_rescans", "cpd_debug_gram_wait", "cpd_synchronize",
            "cpd_batch_create", "cpd_batch_sweep", "cpd_batch_synchronize", "cpd_batch_destroy", "cpd_autotune",
            "cpd_last_error", "cpd_destroy"]
 PHASES = ["pinv", "draw", "probe", "scan", "spmm", "solve", "gram", "sampler", "exact", "clear"]
@@ -72,6 +72,7 @@ def lib():
         "cpd_sweep_kernel_count": ([_P, _P], st),
         "cpd_synchronize": ([_P], st),
         "cpd_sts_rescans": ([_P, _P], st),
+        "cpd_debug_gram_wait": ([_P, i64, i32], st),
         "cpd_batch_create": ([_P, i32, i32, _P, ctypes.POINTER(_P)], st),
         "cpd_batch_sweep": ([_P, i32], st),
         "cpd_batch_synchronize": ([_P], st),
@@ -306,6 +307,12 @@ def cpd_sts_rescans(h):
     n = ctypes.c_int64()
     h._check(lib().cpd_sts_rescans(h.raw, ctypes.cast(ctypes.byref(n), _P)))
     return n.value
+
+
+def cpd_debug_gram_wait(h, wait_cycles, suppress_mma=False):
+    """Test hook: limit of the tensor-core Gram's bounded waits (cycles, 0 =
+    default) and whether it issues its MMAs."""
+    h._check(lib().cpd_debug_gram_wait(h.raw, int(wait_cycles), 1 if suppress_mma else 0))
 
 
 def cpd_synchronize(h):

@@ -528,6 +528,14 @@ cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out) {
   return CPD_OK;
 }
 
+cpd_status cpd_debug_gram_wait(cpd_handle h, int64_t wait_cycles, int32_t suppress_mma) {
+  if (!h || wait_cycles < 0 || (suppress_mma != 0 && suppress_mma != 1)) return CPD_ERR_INVALID_ARG;
+  if (suppress_mma && wait_cycles == 0) return CPD_ERR_INVALID_ARG;   // would wait the full ~2 s
+  h->dbg_gram_wait = wait_cycles;
+  h->dbg_gram_no_mma = suppress_mma;
+  return CPD_OK;
+}
+
 cpd_status cpd_sts_rescans(cpd_handle h, int64_t* out) {
   if (!h || !out) return CPD_ERR_INVALID_ARG;
   cpd_status s = cpd_sts_fallback_count(h, out);

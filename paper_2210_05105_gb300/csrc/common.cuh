@@ -144,6 +144,10 @@ struct cpd_ctx {
   float* dpart = nullptr;              // ceil(sel_cap / 256) x 2 x Rp run partial sums
   uint32_t* dflags = nullptr;          // ceil(sel_cap / 256) chunk flags
 
+  // test hook of the tensor-core Gram's bounded waits (cpd_debug_gram_wait)
+  long long dbg_gram_wait = 0;     // wait limit in clock cycles; 0 = the default (~2 s)
+  int dbg_gram_no_mma = 0;         // 1: issue no MMA, so every wait runs out
+
   // launch shapes chosen by cpd_autotune
   int tune_spmm_bps = 2;    // SpMM blocks per SM (1024 threads each up to 2, then 2048 / bps)
   int hot_cap = 0;          // hot-row slots per mode kept by the layout

@@ -192,12 +192,13 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
 // the row-major tile and adds 16 exact float32 products into 16 independent
 // double-float chains; every GB_FLUSH tiles the chains are added into
 // float64 accumulators, so each df64 chain spans at most GB_FLUSH * TR / nrg
-// rows (error ~ that many 2^-48 of the sum of |terms|).  Each (block, row
+// rows (error ~ that many 2^-48 of the sum of |terms|; the float64 adds run at
+// 1/64 of the float32 rate, so they are kept rare).  Each (block, row
 // group) writes its own float64 partial Gram (gram_reduce_kernel sums them in
 // a fixed order).
-constexpr int GB_FLUSH = 4;
+constexpr int GB_FLUSH = 16;
 constexpr int GB_MAXT = 544;   // threads: one row group of nblk <= 528 blocks (16 independent chains each)
-__global__ void __maxnreg__(120) gram_blk_kernel(
+__global__ void __maxnreg__(112) gram_blk_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int nrg) {
   extern __shared__ float4 gbs4[];

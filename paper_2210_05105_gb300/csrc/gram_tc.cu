@@ -19,7 +19,8 @@
 //
 // Every wait is bounded: a CTA whose MMAs do not complete within ~2 s sets
 // CPD_ERR_TIMEOUT, waits once more (bounded) for them, frees its TMEM and
-// writes a zero partial.
+// writes a zero partial.  (cpd_debug_gram_wait shortens the limit and can
+// suppress the MMAs, so that this path is tested without a fault.)
 #include "common.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -43,7 +44,7 @@ __device__ __forceinline__ uint64_t gt_desc(uint32_t addr, uint32_t lbo, uint32_
          (1ull << 46);
 }
 
-__device__ __forceinline__ bool gt_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool gt_wait(uint32_t bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -55,7 +56,7 @@ __device__ __forceinline__ bool gt_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > GT_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -66,7 +67,7 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
 __global__ void __launch_bounds__(GT_THREADS)
     gram_tc_kernel(const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
                    const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart,
-                   int* __restrict__ status) {
+                   int* __restrict__ status, long long wait_limit, int issue_mma) {
   extern __shared__ __align__(1024) unsigned char gsm[];
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ uint32_t tmem_sh;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(GT_THREADS)
     const int b = it & 1;
     if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x, nxt);
     bool ok = true;
-    if (it >= 2) ok = gt_wait(smem_u32(&mbar[b]), (uint32_t)((it - 2) >> 1) & 1u);   // MMAs of tile it-2 read buffer b
+    if (it >= 2) ok = gt_wait(smem_u32(&mbar[b]), (uint32_t)((it - 2) >> 1) & 1u, wait_limit);   // MMAs of tile it-2 read buffer b
     if (__syncthreads_or(!ok)) { aborted = true; break; }
     unsigned char* buf = gsm + (size_t)b * buf_bytes;
     const int64_t k0 = tile * GT_TK;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(GT_THREADS)
       for (int j = 0; j < 8; ++j) cur[wi][j] = nxt[wi][j];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // generic-proxy stores -> tensor core
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && issue_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t bb = base + (uint32_t)b * buf_bytes;
 #pragma unroll 1
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(GT_THREADS)
   }
   // the last commit covers every MMA this CTA issued
   bool ok = true;
-  if (it > 0) ok = gt_wait(smem_u32(&mbar[(it - 1) & 1]), (uint32_t)((it - 1) >> 1) & 1u);
+  if (it > 0) ok = gt_wait(smem_u32(&mbar[(it - 1) & 1]), (uint32_t)((it - 1) >> 1) & 1u, wait_limit);
   const bool good = !__syncthreads_or(!ok) && !aborted;
   if (!good && t == 0) cpd_set_status(status, CPD_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -291,7 +292,9 @@ cpd_status cpd_gram_tc_launch(cpd_ctx* h, const float* Uin, float* Uout, int64_t
   while (ncols < MT * COLS) ncols <<= 1;
   const int per_sm = std::max(1, std::min(4, 512 / ncols));
   const int grid = std::min(h->num_sms * per_sm, h->gram_blocks);
-  gram_tc_kernel<<<grid, GT_THREADS, shm, h->stream>>>(Uin, Uout, I, h->R, h->Rp, sigma, do_scale, h->Gpart, h->status);
+  const long long limit = h->dbg_gram_wait > 0 ? h->dbg_gram_wait : GT_WAIT_CYCLES;
+  gram_tc_kernel<<<grid, GT_THREADS, shm, h->stream>>>(Uin, Uout, I, h->R, h->Rp, sigma, do_scale, h->Gpart, h->status,
+                                                       limit, h->dbg_gram_no_mma ? 0 : 1);
   CPD_LAUNCH(h, "gram_tc");
   *nblk = grid;
   return CPD_OK;

@@ -131,6 +131,11 @@ WORKLOADS = {
     "zipf_reddit_1B": dict(dims=(8_200_000, 177_000, 8_100_000), nnz=1_000_000_000, zipf=1.3,
                            values="logpoisson", R=100, J=131072, sweeps=20, generator="device",
                            data_seed=1007, init_seed=2007, sample_seed=3007),
+    # the same recipe at a tenth of two dims and 2e7 nonzeros, for ncu captures
+    # of the R = 100 kernels (a few GB on the device)
+    "zipf_reddit_20M": dict(dims=(820_000, 177_000, 810_000), nnz=20_000_000, zipf=1.3,
+                            values="logpoisson", R=100, J=131072, sweeps=20, generator="device",
+                            data_seed=1008, init_seed=2008, sample_seed=3008),
     # 4-mode precision-form workload: values of a planted rank-16 CP model at
     # the drawn coordinates plus Gaussian noise of 10% of their norm (the
     # tensor's zeros are real zeros, so it is not a rank-16 tensor)

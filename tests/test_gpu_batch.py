@@ -58,3 +58,26 @@ def test_autotune_picks_valid_shapes_and_keeps_results():
         assert abs(cpd.cpd_fit(h1) - cpd.cpd_fit(h2)) < 1e-3
         h1.close()
         h2.close()
+
+
+def test_batched_rounds_match_oracle():
+    """The batched graph against the FP64 oracle: two batched ALS rounds of
+    every tensor of the batch (3- and 4-mode, CP-ARLS-LEV and STS-CP) end at
+    the oracle's fit from the same inputs and uniforms (within 1e-3)."""
+    from oracle import cpals as oc
+    cpd = lib_or_build()
+    hs, inputs = [], []
+    for i, (dims, nnz, R, J, m) in enumerate(CASES):
+        idx, vals, init = make_case(dims, nnz, R, seed=500 + i)
+        inputs.append((idx, vals, init))
+        hs.append(create(cpd, dims, idx, vals, init, m, R, J, seed=40 + i))
+    b = cpd.cpd_batch_create(hs, branches=3)
+    cpd.cpd_batch_sweep(b, 2)
+    for i, ((dims, nnz, R, J, m), h, (idx, vals, init)) in enumerate(zip(CASES, hs, inputs)):
+        _, fits = oc.als(idx, vals, dims, [u.astype(np.float64) for u in init], m, 2, J=J, seed=40 + i)
+        f = cpd.cpd_fit(h)
+        print("batched tensor %d (%s, %s): GPU fit %.6f, oracle %.6f" % (i, m, dims, f, fits[-1]))
+        assert abs(f - fits[-1]) < 1e-3
+    b.close()
+    for h in hs:
+        h.close()

@@ -627,3 +627,27 @@ def test_deterministic_capacity_overflow_is_reported(cpd):
                        [torch.from_numpy(u).cuda() for u in init], method="exact", rank=R, samples=J, seed=5,
                        deterministic=True)
     assert ei.value.status == 1
+
+
+def test_tensor_core_gram_wait_runs_out_cleanly(cpd):
+    """The tensor-core Gram's bounded mbarrier waits (precision option 1): with
+    a short limit and no MMA issued, every wait runs out, the kernel latches
+    CPD_ERR_TIMEOUT and frees its tensor memory, and the handle keeps working
+    (the next Gram, with MMAs, equals the oracle's)."""
+    dims, R = (600, 400, 300), 16
+    idx, vals, init = make_case(dims, 20000, R, seed=31)
+    h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                       [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=500, seed=5,
+                       fast=True)
+    U = cpd.cpd_get_factors(h, 0).clone()
+    cpd.cpd_debug_gram_wait(h, 2_000_000, suppress_mma=True)      # ~1 ms at 2 GHz
+    with pytest.raises(cpd.CpdError) as ei:
+        cpd.cpd_set_factors(h, 0, U)
+    assert ei.value.status == 8                                    # CPD_ERR_TIMEOUT
+    cpd.cpd_debug_gram_wait(h, 0, suppress_mma=False)
+    for _ in range(3):                                             # TMEM was freed: allocations succeed
+        cpd.cpd_set_factors(h, 0, U)
+    G = cpd.cpd_get_gram(h, 0).cpu().numpy()
+    ref = oc.gram(U.double().cpu().numpy())
+    assert np.abs(G - ref).max() <= 2e-6 * np.abs(np.diag(ref)).max()
+    h.close()
