@@ -197,12 +197,15 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
 // group) writes its own float64 partial Gram (gram_reduce_kernel sums them in
 // a fixed order).
 constexpr int GB_FLUSH = 16;
-constexpr int GB_MAXT = 544;   // threads: one row group of nblk <= 528 blocks (16 independent chains each)
-__global__ void __maxnreg__(112) gram_blk_kernel(
+constexpr int GB_MAXT = 416;   // threads: one row group of nblk <= 406 blocks (R <= 112), 16 chains each
+__global__ void __launch_bounds__(GB_MAXT, 2) gram_blk_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int nrg) {
   extern __shared__ float4 gbs4[];
-  float* tile = reinterpret_cast<float*>(gbs4);           // TR x Rp, row-major
+  // the float64 flush accumulators live in shared memory (16 per thread, at
+  // [j * blockDim + t] for entry j: conflict-free), the tile after them
+  double* acc64 = reinterpret_cast<double*>(gbs4);
+  float* tile = reinterpret_cast<float*>(acc64 + 16 * blockDim.x);   // TR x Rp, row-major
   __shared__ float inv[CPD_MAX_RANK];
   __shared__ unsigned char ba[CPD_MAX_RANK / 4 * (CPD_MAX_RANK / 4 + 1) / 2];
   __shared__ unsigned char bb[CPD_MAX_RANK / 4 * (CPD_MAX_RANK / 4 + 1) / 2];
@@ -224,11 +227,10 @@ __global__ void __maxnreg__(112) gram_blk_kernel(
   const bool active = rg < nrg;
   const int a0 = 4 * ba[bi], b0 = 4 * bb[bi];
   float ah[4][4], al[4][4];
-  double ad[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { ah[i][j] = 0.0f; al[i][j] = 0.0f; ad[i][j] = 0.0; }
+    for (int j = 0; j < 4; ++j) { ah[i][j] = 0.0f; al[i][j] = 0.0f; acc64[(4 * i + j) * blockDim.x + t] = 0.0; }
   const int64_t ntiles = cpd_ceil_div(I, TR);
   int nt = 0;
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
@@ -262,7 +264,7 @@ __global__ void __maxnreg__(112) gram_blk_kernel(
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            ad[i][j] += df_value(ah[i][j], al[i][j]);
+            acc64[(4 * i + j) * blockDim.x + t] += df_value(ah[i][j], al[i][j]);
             ah[i][j] = 0.0f;
             al[i][j] = 0.0f;
           }
@@ -276,7 +278,8 @@ __global__ void __maxnreg__(112) gram_blk_kernel(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int a = a0 + i, b = b0 + j;
-      if (a <= b && b < R) out[a * R - a * (a - 1) / 2 + (b - a)] = ad[i][j] + df_value(ah[i][j], al[i][j]);
+      if (a <= b && b < R)
+        out[a * R - a * (a - 1) / 2 + (b - a)] = acc64[(4 * i + j) * blockDim.x + t] + df_value(ah[i][j], al[i][j]);
     }
 }
 
@@ -840,30 +843,30 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
 }
 
 // ---- solve for 32 < R <= 128: register-tiled Y (P_hi + P_lo) --------------
-// A block of 256 threads (16 x 16) computes tiles of ST_TM = 128 rows x NB
-// columns (NB = 64 or 128 >= Rp): thread (ty, tx) owns rows 8 ty .. 8 ty + 7
-// and columns TC tx .. TC tx + TC - 1 (TC = NB / 16), 8 TC accumulators in
+// A block of 16 TY threads (TY x 16) computes tiles of 8 TY rows x NB columns
+// (NB = 64 or 128 >= Rp): thread (ty, tx) owns rows 8 ty .. 8 ty + 7 and
+// columns TC tx .. TC tx + TC - 1 (TC = NB / 16), 8 TC accumulators in
 // registers.  G^+ (hi and lo, R x NB, zero past R) stays in shared memory for
-// the whole grid-stride loop; each 128-row tile of Y is staged transposed
-// (K x 128, consecutive lanes loading consecutive rows, so the transposing
-// stores do not conflict).  Per k the thread reads 8 values of Y and TC of
-// each half of G^+ as 16-byte vectors and issues 16 TC FMAs.  Every output
-// adds its terms in the order of solve_kernel:
-// o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
-constexpr int ST_TM = 128;
-constexpr int ST_YS = ST_TM + 4;   // row stride of the transposed Y tile
-template <int NB>
-__global__ void __launch_bounds__(DTHREADS, 1) solve_tile_kernel(
+// the whole grid-stride loop; each tile of Y is staged transposed (Rp x tile
+// rows, consecutive lanes loading consecutive rows, so the transposing stores
+// do not conflict).  Per k the thread reads 8 values of Y and TC of each half
+// of G^+ as 16-byte vectors and issues 16 TC FMAs.  TY = 32 (512 threads,
+// 256-row tiles) where that fits in shared memory, so that 16 warps hide the
+// latency, else TY = 16.  Every output adds its terms in the order of
+// solve_kernel: o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
+template <int NB, int TY>
+__global__ void __launch_bounds__(16 * TY, 1) solve_tile_kernel(
     const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R, int Rp,
     double* __restrict__ colpart) {
   constexpr int TC = NB / 16;
+  constexpr int TM = 8 * TY, YS = TM + 4, NT = 16 * TY;
   extern __shared__ float4 sm4[];
   float* Ph = reinterpret_cast<float*>(sm4);     // R x NB
   float* Pl = Ph + R * NB;                       // R x NB
-  float* Ys = Pl + R * NB;                       // Rp x ST_YS (transposed tile; rows >= R hold Y's zero padding)
-  __shared__ float wsq[16][NB];
+  float* Ys = Pl + R * NB;                       // Rp x YS (transposed tile; rows >= R hold Y's zero padding)
+  __shared__ float wsq[TY][NB];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  for (int e = t; e < R * NB; e += DTHREADS) {
+  for (int e = t; e < R * NB; e += NT) {
     const int a = e / NB, c = e % NB;
     Ph[e] = c < R ? P2[a * R + c] : 0.0f;
     Pl[e] = c < R ? P2[R * R + a * R + c] : 0.0f;
@@ -873,16 +876,16 @@ __global__ void __launch_bounds__(DTHREADS, 1) solve_tile_kernel(
   for (int j = 0; j < TC; ++j) csq[j] = 0.0f;
   const int C4 = Rp / 4;
   const float4* Y4 = reinterpret_cast<const float4*>(Y);
-  for (int64_t r0 = (int64_t)blockIdx.x * ST_TM; r0 < I; r0 += (int64_t)gridDim.x * ST_TM) {
+  for (int64_t r0 = (int64_t)blockIdx.x * TM; r0 < I; r0 += (int64_t)gridDim.x * TM) {
     __syncthreads();                             // previous tile consumed (and G^+ staged)
     // lanes take consecutive rows of one float4 column of the tile
-    for (int e = t; e < ST_TM * C4; e += DTHREADS) {
-      const int row = e % ST_TM, c4 = e / ST_TM;
+    for (int e = t; e < TM * C4; e += NT) {
+      const int row = e % TM, c4 = e / TM;
       const float4 v = (r0 + row < I) ? Y4[(r0 + row) * C4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
-      Ys[(4 * c4 + 0) * ST_YS + row] = v.x;
-      Ys[(4 * c4 + 1) * ST_YS + row] = v.y;
-      Ys[(4 * c4 + 2) * ST_YS + row] = v.z;
-      Ys[(4 * c4 + 3) * ST_YS + row] = v.w;
+      Ys[(4 * c4 + 0) * YS + row] = v.x;
+      Ys[(4 * c4 + 1) * YS + row] = v.y;
+      Ys[(4 * c4 + 2) * YS + row] = v.z;
+      Ys[(4 * c4 + 3) * YS + row] = v.w;
     }
     __syncthreads();
     float acc[8][TC];
@@ -892,8 +895,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) solve_tile_kernel(
       for (int j = 0; j < TC; ++j) acc[i][j] = 0.0f;
 #pragma unroll 2
     for (int a = 0; a < R; ++a) {
-      const float4 y0 = *reinterpret_cast<const float4*>(Ys + a * ST_YS + 8 * ty);
-      const float4 y1 = *reinterpret_cast<const float4*>(Ys + a * ST_YS + 8 * ty + 4);
+      const float4 y0 = *reinterpret_cast<const float4*>(Ys + a * YS + 8 * ty);
+      const float4 y1 = *reinterpret_cast<const float4*>(Ys + a * YS + 8 * ty + 4);
       const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
       float ph[TC], pl[TC];
 #pragma unroll
@@ -929,16 +932,17 @@ __global__ void __launch_bounds__(DTHREADS, 1) solve_tile_kernel(
 #pragma unroll
   for (int j = 0; j < TC; ++j) wsq[ty][TC * tx + j] = csq[j];
   __syncthreads();
-  for (int c = t; c < R; c += DTHREADS) {
+  for (int c = t; c < R; c += NT) {
     double s = 0.0;
-    for (int y = 0; y < 16; ++y) s += (double)wsq[y][c];
+    for (int y = 0; y < TY; ++y) s += (double)wsq[y][c];
     colpart[(int64_t)blockIdx.x * R + c] = s;
   }
 }
 
-static size_t solve_tile_smem(int R, int NB) {
-  return ((size_t)2 * R * NB + (size_t)cpd_pad4(R) * ST_YS) * sizeof(float);
+static size_t solve_tile_smem(int R, int NB, int TY) {
+  return ((size_t)2 * R * NB + (size_t)cpd_pad4(R) * (8 * TY + 4)) * sizeof(float);
 }
+static int solve_tile_ty(int R, int NB) { return solve_tile_smem(R, NB, 32) + NB * 32 * 4 <= 220 * 1024 ? 32 : 16; }
 
 static int solve_rb(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
 
@@ -1030,16 +1034,15 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
   }
   size_t shm = (size_t)TRP * R * sizeof(float);
   const int npairs = R * (R + 1) / 2;
-  if (R > 64 && !h->opt.precision) {
+  if (R > 64 && !h->opt.precision && (h->Rp / 4) * (h->Rp / 4 + 1) / 2 <= GB_MAXT) {
     // register-blocked kernel: (4x4 blocks of the upper block triangle) x row
     // groups per CTA, one CTA per SM, one partial per (CTA, row group)
     const int nb4 = h->Rp / 4, nblk = nb4 * (nb4 + 1) / 2;
     const int nrg = 1;
     if (nblk > GB_MAXT) return cpd_fail(h, CPD_ERR_INVALID_ARG, "Gram block triangle exceeds the kernel's block size");
-    const int grid = std::max(1, std::min(h->num_sms, h->gram_blocks / nrg));
-    gram_blk_kernel<<<grid, nblk * nrg, (size_t)TR * h->Rp * sizeof(float), h->stream>>>(Uin, Uout, I, R, h->Rp,
-                                                                                          sigma, do_scale, h->Gpart,
-                                                                                          nrg);
+    const int grid = std::max(1, std::min(2 * h->num_sms, h->gram_blocks / nrg));   // two CTAs per SM
+    const size_t gshm = (size_t)16 * nblk * nrg * sizeof(double) + (size_t)TR * h->Rp * sizeof(float);
+    gram_blk_kernel<<<grid, nblk * nrg, gshm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale, h->Gpart, nrg);
     CPD_LAUNCH(h, "gram_blk");
     gram_reduce_kernel<<<std::max(1, (npairs + 7) / 8), 256, 0, h->stream>>>(h->Gpart, grid * nrg, R, G);
     CPD_LAUNCH(h, "gram_reduce");
@@ -1142,14 +1145,18 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     } else if (rb == 16)
       solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else {
-      // one 256-thread block per SM (the tile and G^+ fill most of its shared memory)
-      nblk = (int)std::min<int64_t>(h->num_sms, std::max<int64_t>(cpd_ceil_div(I, ST_TM), 1));
-      if (rb == 64)
-        solve_tile_kernel<64><<<nblk, DTHREADS, solve_tile_smem(R, 64), h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I,
-                                                                                     R, h->Rp, h->colsq);
+      // one block per SM (the tile and G^+ fill most of its shared memory)
+      const int nb = rb == 64 ? 64 : 128, ty = solve_tile_ty(R, nb);
+      nblk = (int)std::min<int64_t>(h->num_sms, std::max<int64_t>(cpd_ceil_div(I, 8 * ty), 1));
+      const size_t sh = solve_tile_smem(R, nb, ty);
+      if (nb == 64 && ty == 32)
+        solve_tile_kernel<64, 32><<<nblk, 512, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
+      else if (nb == 64)
+        solve_tile_kernel<64, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
+      else if (ty == 32)
+        solve_tile_kernel<128, 32><<<nblk, 512, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
       else
-        solve_tile_kernel<128><<<nblk, DTHREADS, solve_tile_smem(R, 128), h->stream>>>(Y, h->Gnpinv_split, h->Uwork,
-                                                                                       I, R, h->Rp, h->colsq);
+        solve_tile_kernel<128, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     }
     CPD_LAUNCH(h, "solve");
     sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, nblk, R, h->sigma);
@@ -1191,8 +1198,11 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
       {(const void*)normalize_gram_kernel<9>, s1}, {(const void*)normalize_gram_kernel<33>, s1},
       {(const void*)pinv_kernel, s2},              {(const void*)solve_kernel<16>, s3},
       {(const void*)solve_kernel<32>, s3},
-      {(const void*)solve_tile_kernel<64>, solve_tile_smem(std::min(R, 64), 64)},
-      {(const void*)solve_tile_kernel<128>, solve_tile_smem(R, 128)}};
+      {(const void*)gram_blk_kernel, (size_t)16 * GB_MAXT * sizeof(double) + (size_t)TR * CPD_MAX_RANK * sizeof(float)},
+      {(const void*)solve_tile_kernel<64, 32>, solve_tile_smem(std::min(R, 64), 64, 32)},
+      {(const void*)solve_tile_kernel<64, 16>, solve_tile_smem(std::min(R, 64), 64, 16)},
+      {(const void*)solve_tile_kernel<128, 32>, std::min<size_t>(solve_tile_smem(R, 128, 32), 227 * 1024)},
+      {(const void*)solve_tile_kernel<128, 16>, solve_tile_smem(R, 128, 16)}};
   for (const auto& a : attrs) {
     const cpd_status st = cpd_smem_attr(h, a.first, a.second);
     if (st != CPD_OK) return st;

@@ -24,16 +24,20 @@ constexpr int LEV_THREADS = 256;
 // ~2^-48 relative instead of float64 FMAs at 1/64 rate.  Also writes the sum
 // of each block's scores.  (The tile's row stride 257 keeps the transposing
 // stores free of bank conflicts.)
-// SPLIT threads share a row (blockDim = SPLIT * LEV_THREADS): thread part h
-// takes rows a = h, h + SPLIT, ... of the triangle, and part 0 merges the
-// partial double-floats in part order (deterministic).  Large R gives each
-// row R(R+1)/2 terms while the transposed tile limits a block per SM, so the
-// split supplies the warps that hide the df64 chains' latency.
-template <int SPLIT>
-__global__ void __launch_bounds__(LEV_THREADS * SPLIT) lev_kernel(const float* __restrict__ U, int64_t I, int R,
-                                                                  int Rp, const double* __restrict__ X,
-                                                                  double* __restrict__ ell, double* __restrict__ blk,
-                                                                  int fast) {
+// SPLIT threads share a row: thread part h takes rows a = h, h + SPLIT, ...
+// of the triangle, and part 0 merges the partial double-floats in part order
+// (deterministic).  With ROWS = 2 a thread carries rows t and t + 128 of the
+// block's 256, so each coefficient load and the loop control serve two rows
+// (blockDim = SPLIT * LEV_THREADS / ROWS).  Large R gives each row R(R+1)/2
+// terms while the transposed tile limits a block per SM, so the split
+// supplies the warps that hide the df64 chains' latency.
+template <int SPLIT, int ROWS>
+__global__ void __launch_bounds__(LEV_THREADS / ROWS * SPLIT) lev_kernel(const float* __restrict__ U, int64_t I,
+                                                                         int R, int Rp, const double* __restrict__ X,
+                                                                         double* __restrict__ ell,
+                                                                         double* __restrict__ blk, int fast) {
+  constexpr int RT = LEV_THREADS / ROWS;           // row slots per part
+  constexpr int NT = RT * SPLIT;
   extern __shared__ float4 lsm4[];
   const int npairs = R * (R + 1) / 2;
   float2* Xs = reinterpret_cast<float2*>(lsm4);                 // npairs (hi, lo), row-major upper triangle
@@ -41,8 +45,8 @@ __global__ void __launch_bounds__(LEV_THREADS * SPLIT) lev_kernel(const float* _
   __shared__ double red[LEV_THREADS / 32];
   __shared__ float2 partial[SPLIT > 1 ? SPLIT - 1 : 1][LEV_THREADS];
   const int tid = threadIdx.x;
-  const int t = tid % LEV_THREADS, h = tid / LEV_THREADS;
-  for (int p = tid; p < npairs; p += LEV_THREADS * SPLIT) {
+  const int t = tid % RT, h = tid / RT;
+  for (int p = tid; p < npairs; p += NT) {
     int a = 0, rem = p;
     while (rem >= R - a) { rem -= R - a; ++a; }
     const int b = a + rem;
@@ -51,102 +55,98 @@ __global__ void __launch_bounds__(LEV_THREADS * SPLIT) lev_kernel(const float* _
     Xs[p] = make_float2(hi, (float)(x - (double)hi));
   }
   const int64_t r0 = (int64_t)blockIdx.x * LEV_THREADS;
-  for (int e = tid; e < LEV_THREADS * Rp; e += LEV_THREADS * SPLIT) {   // coalesced rows -> transposed tile
+  for (int e = tid; e < LEV_THREADS * Rp; e += NT) {   // coalesced rows -> transposed tile
     const int rr = e / Rp, c = e % Rp;
     us[c * (LEV_THREADS + 1) + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
   }
   __syncthreads();
-  const int64_t i = r0 + t;
-  float lh = 0.0f, ll = 0.0f;
-  if (i < I) {
-    if (fast) {                          // float32 (precision option 1), two chains
-      float l2 = 0.0f;
-      for (int a = h; a < R; a += SPLIT) {
-        int p = a * R - a * (a - 1) / 2;
-        const float ua = us[a * (LEV_THREADS + 1) + t];
-        int b = a;
-        for (; b + 1 < R; b += 2, p += 2) {
-          lh = fmaf(ua * us[b * (LEV_THREADS + 1) + t], Xs[p].x, lh);
-          l2 = fmaf(ua * us[(b + 1) * (LEV_THREADS + 1) + t], Xs[p + 1].x, l2);
-        }
-        if (b < R) { lh = fmaf(ua * us[b * (LEV_THREADS + 1) + t], Xs[p].x, lh); ++p; }
+  // rows t + q RT of the block, q < ROWS
+  float lh[ROWS], ll[ROWS];
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) { lh[q] = 0.0f; ll[q] = 0.0f; }
+  if (fast) {                          // float32 (precision option 1)
+    for (int a = h; a < R; a += SPLIT) {
+      int p = a * R - a * (a - 1) / 2;
+      float ua[ROWS];
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) ua[q] = us[a * (LEV_THREADS + 1) + t + q * RT];
+      for (int b = a; b < R; ++b, ++p) {
+        const float x = Xs[p].x;
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) lh[q] = fmaf(ua[q] * us[b * (LEV_THREADS + 1) + t + q * RT], x, lh[q]);
       }
-      lh += l2;
-    } else {
-      // two independent df64 chains (even and odd b) for instruction-level
-      // parallelism, four when the row is split (large R: fewer warps); merged
-      // at the end
-      float lh2 = 0.0f, ll2 = 0.0f;
-      for (int a = h; a < R; a += SPLIT) {
-        int p = a * R - a * (a - 1) / 2;
-        const float ua = us[a * (LEV_THREADS + 1) + t];
-        int b = a;
-        if (SPLIT > 1) {
-          float lh3 = 0.0f, ll3 = 0.0f, lh4 = 0.0f, ll4 = 0.0f;
-          for (; b + 3 < R; b += 4, p += 4) {
-            const float ub0 = us[b * (LEV_THREADS + 1) + t], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t];
-            const float ub2 = us[(b + 2) * (LEV_THREADS + 1) + t], ub3 = us[(b + 3) * (LEV_THREADS + 1) + t];
-            const float2 x0 = Xs[p], x1 = Xs[p + 1], x2 = Xs[p + 2], x3 = Xs[p + 3];
-            const float ph0 = __fmul_rn(ua, ub0), ph1 = __fmul_rn(ua, ub1);
-            const float ph2 = __fmul_rn(ua, ub2), ph3 = __fmul_rn(ua, ub3);
-            const float pl0 = __fmaf_rn(ua, ub0, -ph0), pl1 = __fmaf_rn(ua, ub1, -ph1);
-            const float pl2 = __fmaf_rn(ua, ub2, -ph2), pl3 = __fmaf_rn(ua, ub3, -ph3);
-            df_fma(lh, ll, ph0, x0.x);
-            df_fma(lh2, ll2, ph1, x1.x);
-            df_fma(lh3, ll3, ph2, x2.x);
-            df_fma(lh4, ll4, ph3, x3.x);
-            ll = __fmaf_rn(pl0, x0.x, __fmaf_rn(ph0, x0.y, ll));
-            ll2 = __fmaf_rn(pl1, x1.x, __fmaf_rn(ph1, x1.y, ll2));
-            ll3 = __fmaf_rn(pl2, x2.x, __fmaf_rn(ph2, x2.y, ll3));
-            ll4 = __fmaf_rn(pl3, x3.x, __fmaf_rn(ph3, x3.y, ll4));
-          }
-          df_merge(lh3, ll3, lh4, ll4);
-          df_merge(lh2, ll2, lh3, ll3);
-        }
-        for (; b + 1 < R; b += 2, p += 2) {
-          const float ub0 = us[b * (LEV_THREADS + 1) + t], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t];
-          const float2 x0 = Xs[p], x1 = Xs[p + 1];
-          const float ph0 = __fmul_rn(ua, ub0), ph1 = __fmul_rn(ua, ub1);
-          const float pl0 = __fmaf_rn(ua, ub0, -ph0), pl1 = __fmaf_rn(ua, ub1, -ph1);
-          df_fma(lh, ll, ph0, x0.x);
-          df_fma(lh2, ll2, ph1, x1.x);
-          ll = __fmaf_rn(pl0, x0.x, __fmaf_rn(ph0, x0.y, ll));
-          ll2 = __fmaf_rn(pl1, x1.x, __fmaf_rn(ph1, x1.y, ll2));
-        }
-        if (b < R) {
-          const float ub = us[b * (LEV_THREADS + 1) + t];
-          const float2 x = Xs[p];
-          const float ph = __fmul_rn(ua, ub);
-          const float pl = __fmaf_rn(ua, ub, -ph);
-          df_fma(lh, ll, ph, x.x);
-          ll = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll));
-        }
-      }
-      df_merge(lh, ll, lh2, ll2);
     }
+  } else {
+    // per row two independent df64 chains (even and odd b) for
+    // instruction-level parallelism, merged at the end
+    float lh2[ROWS], ll2[ROWS];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) { lh2[q] = 0.0f; ll2[q] = 0.0f; }
+    for (int a = h; a < R; a += SPLIT) {
+      int p = a * R - a * (a - 1) / 2;
+      float ua[ROWS];
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) ua[q] = us[a * (LEV_THREADS + 1) + t + q * RT];
+      int b = a;
+      for (; b + 1 < R; b += 2, p += 2) {
+        const float2 x0 = Xs[p], x1 = Xs[p + 1];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+          const float ub0 = us[b * (LEV_THREADS + 1) + t + q * RT], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t + q * RT];
+          const float ph0 = __fmul_rn(ua[q], ub0), ph1 = __fmul_rn(ua[q], ub1);
+          const float pl0 = __fmaf_rn(ua[q], ub0, -ph0), pl1 = __fmaf_rn(ua[q], ub1, -ph1);
+          df_fma(lh[q], ll[q], ph0, x0.x);
+          df_fma(lh2[q], ll2[q], ph1, x1.x);
+          ll[q] = __fmaf_rn(pl0, x0.x, __fmaf_rn(ph0, x0.y, ll[q]));
+          ll2[q] = __fmaf_rn(pl1, x1.x, __fmaf_rn(ph1, x1.y, ll2[q]));
+        }
+      }
+      if (b < R) {
+        const float2 x = Xs[p];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+          const float ub = us[b * (LEV_THREADS + 1) + t + q * RT];
+          const float ph = __fmul_rn(ua[q], ub);
+          const float pl = __fmaf_rn(ua[q], ub, -ph);
+          df_fma(lh[q], ll[q], ph, x.x);
+          ll[q] = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll[q]));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) df_merge(lh[q], ll[q], lh2[q], ll2[q]);
   }
   if (SPLIT > 1) {
-    if (h > 0) partial[h - 1][t] = make_float2(lh, ll);
+    if (h > 0)
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) partial[h - 1][t + q * RT] = make_float2(lh[q], ll[q]);
     __syncthreads();
     if (h == 0)
-      for (int q = 0; q < SPLIT - 1; ++q) {
-        const float2 o = partial[q][t];
-        if (fast) lh += o.x; else df_merge(lh, ll, o.x, o.y);
-      }
+      for (int g = 0; g < SPLIT - 1; ++g)
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+          const float2 o = partial[g][t + q * RT];
+          if (fast) lh[q] += o.x; else df_merge(lh[q], ll[q], o.x, o.y);
+        }
   }
   if (h > 0) return;
-  double l = 0.0;
-  if (i < I) {
-    l = df_value(lh, ll);
-    ell[i] = l;
+  double lsum = 0.0;
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) {
+    const int64_t i = r0 + t + q * RT;
+    if (i < I) {
+      const double l = df_value(lh[q], ll[q]);
+      ell[i] = l;
+      lsum += l;
+    }
   }
-  // block sum in a fixed order (the first LEV_THREADS threads)
-  double s = warp_sum(l);
-  if ((t & 31) == 0) red[t >> 5] = s;
-  asm volatile("bar.sync 1, %0;" ::"n"(LEV_THREADS));
+  // block sum in a fixed order (the RT threads of part 0)
+  double sw = warp_sum(lsum);
+  if ((t & 31) == 0) red[t >> 5] = sw;
+  asm volatile("bar.sync 1, %0;" ::"n"(RT));
   if (t == 0) {
     double b = 0.0;
-    for (int w = 0; w < LEV_THREADS / 32; ++w) b += red[w];
+    for (int w = 0; w < RT / 32; ++w) b += red[w];
     blk[blockIdx.x] = b;
   }
 }
@@ -282,21 +282,21 @@ size_t lev_smem(int R) {
   return (size_t)npairs * 8 + (size_t)(LEV_THREADS + 1) * cpd_pad4(R) * 4;
 }
 
-int lev_split(int R) { return R > 64 ? 4 : R > 32 ? 2 : 1; }
+int lev_split(int R) { return R > 64 ? 8 : R > 32 ? 4 : 1; }
 
 cpd_status quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
                         double* cdf) {
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
   const int sp = lev_split(h->R);
-  if (sp == 4)
-    lev_kernel<4><<<(unsigned)nb, LEV_THREADS * 4, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
-                                                                               h->opt.precision);
-  else if (sp == 2)
-    lev_kernel<2><<<(unsigned)nb, LEV_THREADS * 2, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
-                                                                               h->opt.precision);
+  if (sp == 8)          // R > 64: two rows a thread, 8 parts
+    lev_kernel<8, 2><<<(unsigned)nb, LEV_THREADS / 2 * 8, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                                      h->opt.precision);
+  else if (sp == 4)     // 32 < R <= 64
+    lev_kernel<4, 2><<<(unsigned)nb, LEV_THREADS / 2 * 4, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                                      h->opt.precision);
   else
-    lev_kernel<1><<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
-                                                                           h->opt.precision);
+    lev_kernel<1, 1><<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+                                                                              h->opt.precision);
   CPD_LAUNCH(h, "lev");
   cdf_kernel<<<(unsigned)nb, LEV_THREADS, 0, h->stream>>>(q, I, blk, cdf);
   CPD_LAUNCH(h, "cdf");
@@ -320,7 +320,7 @@ cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double*
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
 // once, outside any stream capture).
 cpd_status cpd_sample_init(cpd_ctx* h) {
-  for (const void* f : {(const void*)lev_kernel<1>, (const void*)lev_kernel<2>, (const void*)lev_kernel<4>}) {
+  for (const void* f : {(const void*)lev_kernel<1, 1>, (const void*)lev_kernel<4, 2>, (const void*)lev_kernel<8, 2>}) {
     const cpd_status st_ = cpd_smem_attr(h, f, lev_smem(h->R));
     if (st_ != CPD_OK) return st_;
   }

@@ -51,6 +51,8 @@ def test_arls_sampler_state_matches_oracle(cpd, R, dims):
     h, idx, vals, init, cfg = _small(cpd, R=R, dims=dims)
     fs = gpu_factors(cpd, h)
     for k in range(3):
+        # the Gram behind the scores: df64 kernels (register-blocked for R > 64)
+        assert rel_frob(cpd.cpd_get_gram(h, k).cpu().numpy(), oc.gram(fs[k])) < 1e-13
         st = oc.arls_build(fs[k])
         ell, cdf = cpd.cpd_get_arls_state(h, k)
         assert np.max(np.abs(ell.cpu().numpy() - st["ell"]) / st["ell"].max()) < 1e-12
