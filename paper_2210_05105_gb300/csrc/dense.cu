@@ -850,9 +850,7 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
 // the whole grid-stride loop; each tile of Y is staged transposed (Rp x tile
 // rows, consecutive lanes loading consecutive rows, so the transposing stores
 // do not conflict).  Per k the thread reads 8 values of Y and TC of each half
-// of G^+ as 16-byte vectors and issues 16 TC FMAs.  TY = 32 (512 threads,
-// 256-row tiles) where that fits in shared memory, so that 16 warps hide the
-// latency, else TY = 16.  Every output adds its terms in the order of
+// of G^+ as 16-byte vectors and issues 16 TC FMAs.  Every output adds its terms in the order of
 // solve_kernel: o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
 template <int NB, int TY>
 __global__ void __launch_bounds__(16 * TY, 1) solve_tile_kernel(
@@ -942,7 +940,10 @@ __global__ void __launch_bounds__(16 * TY, 1) solve_tile_kernel(
 static size_t solve_tile_smem(int R, int NB, int TY) {
   return ((size_t)2 * R * NB + (size_t)cpd_pad4(R) * (8 * TY + 4)) * sizeof(float);
 }
-static int solve_tile_ty(int R, int NB) { return solve_tile_smem(R, NB, 32) + NB * 32 * 4 <= 220 * 1024 ? 32 : 16; }
+// 256-row tiles of 512 threads were measured slower than 128-row tiles of
+// 256 threads at R = 100 (22.6 against 20.0 ms a round at the billion-scale
+// workload), so TY = 16 is used throughout
+static int solve_tile_ty(int R, int NB) { (void)R; (void)NB; return 16; }
 
 static int solve_rb(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
 
@@ -1149,12 +1150,8 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
       const int nb = rb == 64 ? 64 : 128, ty = solve_tile_ty(R, nb);
       nblk = (int)std::min<int64_t>(h->num_sms, std::max<int64_t>(cpd_ceil_div(I, 8 * ty), 1));
       const size_t sh = solve_tile_smem(R, nb, ty);
-      if (nb == 64 && ty == 32)
-        solve_tile_kernel<64, 32><<<nblk, 512, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
-      else if (nb == 64)
+      if (nb == 64)
         solve_tile_kernel<64, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
-      else if (ty == 32)
-        solve_tile_kernel<128, 32><<<nblk, 512, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
       else
         solve_tile_kernel<128, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     }
@@ -1199,9 +1196,7 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
       {(const void*)pinv_kernel, s2},              {(const void*)solve_kernel<16>, s3},
       {(const void*)solve_kernel<32>, s3},
       {(const void*)gram_blk_kernel, (size_t)16 * GB_MAXT * sizeof(double) + (size_t)TR * CPD_MAX_RANK * sizeof(float)},
-      {(const void*)solve_tile_kernel<64, 32>, solve_tile_smem(std::min(R, 64), 64, 32)},
       {(const void*)solve_tile_kernel<64, 16>, solve_tile_smem(std::min(R, 64), 64, 16)},
-      {(const void*)solve_tile_kernel<128, 32>, std::min<size_t>(solve_tile_smem(R, 128, 32), 227 * 1024)},
       {(const void*)solve_tile_kernel<128, 16>, solve_tile_smem(R, 128, 16)}};
   for (const auto& a : attrs) {
     const cpd_status st = cpd_smem_attr(h, a.first, a.second);
