@@ -210,19 +210,25 @@ def inverse_cdf(cdf, ell, t):
 
 
 def gram_condition(Gk):
-    """2-norm condition number lambda_max / lambda_min of a symmetric PSD
-    Gram from its eigenvalues (inf when singular)."""
-    lam = np.linalg.eigvalsh(0.5 * (np.asarray(Gk) + np.asarray(Gk).T))
-    return float(lam[-1] / lam[0]) if lam[0] > 0 else float("inf")
+    """Condition number of the pseudo-inverse of a symmetric PSD Gram (Eq. 4):
+    lambda_max over the smallest eigenvalue that pinv_sym keeps (above
+    R 2^-52 lambda_max); 1 for a zero Gram."""
+    G = np.asarray(Gk, dtype=np.float64)
+    lam = np.linalg.eigvalsh(0.5 * (G + G.T))
+    lmax = float(np.max(np.abs(lam))) if lam.size else 0.0
+    kept = lam[lam > G.shape[0] * 2.0 ** -52 * lmax]
+    return float(lmax / kept[0]) if kept.size else 1.0
 
 
-def arls_tie_tolerance(sampler, floor=1e-12):
+def arls_tie_tolerance(sampler, floor=1e-12, cap=1e-6):
     """Tie window of a CP-ARLS-LEV draw on factor k, relative to C_k: a float64
     Gram is known to 2^-53 of its entries, so G_k^+ -- and every leverage
     score and running sum built on it -- is determined only to about
     cond(G_k) 2^-53 relative, whatever the arithmetic that follows.  The
-    window is max(floor, 8 cond(G_k) 2^-53)."""
-    return max(floor, 8.0 * gram_condition(sampler["G"]) * 2.0 ** -53)
+    window is max(floor, 8 cond(G_k) 2^-53), capped at `cap`: past it the
+    scores of a nearly singular Gram are fixed by the pseudo-inverse's cutoff,
+    which both sides apply alike, and agreement is checked as such."""
+    return min(cap, max(floor, 8.0 * gram_condition(sampler["G"]) * 2.0 ** -53))
 
 
 def arls_draw(samplers, n, J, seed, sweep, tie_tol=1e-12):

@@ -8,12 +8,16 @@
 // S = [hi^T; mid^T; lo^T] (3 Rp rows, K running over the rows of U), the MMA
 // computes D = S S^T and G[a][b] is the sum of the 3 x 3 piece blocks of D.
 //
-// Per CTA (up to four per SM, persistent over 64-row tiles of U): all threads load a
-// tile (scaled by 1 / sigma when renormalising, the scaled values written back
-// as the new factor), split it and store the pieces in the no-swizzle K-major
-// core-matrix layout (8 rows x 16 bytes per core matrix); one thread issues
-// the MMAs and commits them to an mbarrier.  Two operand buffers let the next
-// tile be staged while the tensor core reads the previous one.  At the end the
+// Per CTA (up to four per SM, persistent over 64-row tiles of U): one thread
+// fetches each 64-row tile of U into shared memory with the Tensor Memory
+// Accelerator (a 2D tensor map over U, cp.async.bulk.tensor, completion on an
+// mbarrier; the next tile is in flight while the current one is staged);
+// all threads then scale it (by 1 / sigma when renormalising, the scaled
+// values written back as the new factor), split it and store the pieces in
+// the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix); one thread issues the MMAs and commits them to an mbarrier.  Two
+// operand buffers let the next tile be staged while the tensor core reads the
+// previous one.  At the end the
 // accumulator is read with tcgen05.ld, the piece blocks are summed and the
 // CTA's float64 partial Gram is written (reduced by gram_reduce_kernel).
 //
@@ -22,8 +26,10 @@
 // writes a zero partial.  (cpd_debug_gram_wait shortens the limit and can
 // suppress the MMAs, so that this path is tested without a fault.)
 #include "common.cuh"
+#include <cuda.h>           // CUtensorMap and cuTensorMapEncodeTiled's types (called through the runtime's entry point)
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <mutex>
 
 namespace {
 
@@ -65,11 +71,12 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
 }
 
 __global__ void __launch_bounds__(GT_THREADS)
-    gram_tc_kernel(const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
-                   const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart,
-                   int* __restrict__ status, long long wait_limit, int issue_mma) {
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ Uin, float* __restrict__ Uout,
+                   int64_t I, int R, int Rp, const double* __restrict__ sigma, int do_scale,
+                   double* __restrict__ gpart, int* __restrict__ status, long long wait_limit, int issue_mma) {
   extern __shared__ __align__(1024) unsigned char gsm[];
   __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ __align__(8) unsigned long long tbar[2];      // TMA tile arrivals
   __shared__ uint32_t tmem_sh;
   __shared__ float inv[CPD_MAX_RANK];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -81,6 +88,10 @@ __global__ void __launch_bounds__(GT_THREADS)
   uint32_t ncols = 32;
   while (ncols < (uint32_t)(MT * COLS)) ncols <<= 1;
   const bool write_back = Uout != Uin || do_scale;
+  // raw float32 tiles (GT_TK x Rp, row-major as in U) written by the TMA,
+  // after the two operand buffers
+  float* raw = reinterpret_cast<float*>(gsm + 2 * (size_t)buf_bytes);
+  const uint32_t raw_bytes = (uint32_t)GT_TK * (uint32_t)Rp * 4u;
 
   for (int r = t; r < CPD_MAX_RANK; r += GT_THREADS) {
     const double s = (do_scale && r < R) ? sigma[r] : 0.0;
@@ -90,6 +101,8 @@ __global__ void __launch_bounds__(GT_THREADS)
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -110,32 +123,32 @@ __global__ void __launch_bounds__(GT_THREADS)
   const int64_t ntiles = (I + GT_TK - 1) / GT_TK;
 
   // the thread's work items (column r, 8-row group kg) of a tile: at most
-  // GT_MAXW; the next tile's values are loaded while the current one is
-  // split and stored (register double buffering hides the load latency)
+  // GT_MAXW.  Tile tl goes to raw buffer tl's iteration parity: thread 0 arms
+  // the buffer's mbarrier with the tile's byte count and issues the copy
+  // (rows past I arrive as zeros: the tensor map's out-of-bounds fill).
   const int nwork = Rp * (int)GT_KC;
-  float cur[GT_MAXW][8], nxt[GT_MAXW][8];
-  auto load_tile = [&](int64_t tl, float (&dst)[GT_MAXW][8]) {
-#pragma unroll
-    for (int wi = 0; wi < GT_MAXW; ++wi) {
-      const int w = t + wi * GT_THREADS;
-      const int r = w % Rp, kg = w / Rp;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t k = tl * GT_TK + kg * 8 + j;
-        dst[wi][j] = (w < nwork && k < I && r < R) ? Uin[k * Rp + r] : 0.0f;
-      }
-    }
+  auto fetch_tile = [&](int64_t tl, int rb) {
+    const uint32_t bar = smem_u32(&tbar[rb]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(raw_bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(raw + (size_t)rb * GT_TK * Rp)),
+        "l"(&tmap), "r"(0), "r"((int)(tl * GT_TK)), "r"(bar)
+        : "memory");
   };
-  if ((int64_t)blockIdx.x < ntiles) load_tile(blockIdx.x, cur);
+  if (t == 0 && (int64_t)blockIdx.x < ntiles) fetch_tile(blockIdx.x, 0);
 
   int it = 0;
   bool aborted = false;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int b = it & 1;
-    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x, nxt);
-    bool ok = true;
-    if (it >= 2) ok = gt_wait(smem_u32(&mbar[b]), (uint32_t)((it - 2) >> 1) & 1u, wait_limit);   // MMAs of tile it-2 read buffer b
+    // the next tile's copy goes into the other raw buffer, consumed one
+    // iteration ago (every thread passed the barrier after its staging)
+    if (t == 0 && tile + gridDim.x < ntiles) fetch_tile(tile + gridDim.x, b ^ 1);
+    bool ok = gt_wait(smem_u32(&tbar[b]), (uint32_t)(it >> 1) & 1u, wait_limit);       // this tile has arrived
+    if (ok && it >= 2) ok = gt_wait(smem_u32(&mbar[b]), (uint32_t)((it - 2) >> 1) & 1u, wait_limit);   // MMAs of tile it-2 read buffer b
     if (__syncthreads_or(!ok)) { aborted = true; break; }
+    const float* rt = raw + (size_t)b * GT_TK * Rp;
     unsigned char* buf = gsm + (size_t)b * buf_bytes;
     const int64_t k0 = tile * GT_TK;
 #pragma unroll
@@ -150,7 +163,7 @@ __global__ void __launch_bounds__(GT_THREADS)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int64_t k = k0 + kg * 8 + j + q;
-          const float x = cur[wi][j + q] * inv[r];
+          const float x = (r < R ? rt[(kg * 8 + j + q) * Rp + r] : 0.0f) * inv[r];
           if (write_back && k < I) Uout[k * Rp + r] = x;
           v[q] = x;
         }
@@ -177,10 +190,6 @@ __global__ void __launch_bounds__(GT_THREADS)
         *reinterpret_cast<uint4*>(buf + ((uint32_t)(m >> 3) * GT_KC + (uint32_t)kg) * 128u + (uint32_t)(m & 7) * 16u) = val;
       }
     }
-#pragma unroll
-    for (int wi = 0; wi < GT_MAXW; ++wi)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) cur[wi][j] = nxt[wi][j];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // generic-proxy stores -> tensor core
     __syncthreads();
     if (t == 0 && issue_mma) {
@@ -208,6 +217,14 @@ __global__ void __launch_bounds__(GT_THREADS)
   // the last commit covers every MMA this CTA issued
   bool ok = true;
   if (it > 0) ok = gt_wait(smem_u32(&mbar[(it - 1) & 1]), (uint32_t)((it - 1) >> 1) & 1u, wait_limit);
+  // an aborted CTA may have a tile copy in flight (issued for iteration it +
+  // 1 or not yet waited for at it): wait for it, bounded, before the buffers
+  // are reused or the CTA exits
+  if (aborted && t == 0) {
+    const int64_t cur_tile = (int64_t)blockIdx.x + (int64_t)it * gridDim.x;
+    gt_wait(smem_u32(&tbar[it & 1]), (uint32_t)(it >> 1) & 1u, wait_limit);
+    if (cur_tile + gridDim.x < ntiles) gt_wait(smem_u32(&tbar[(it + 1) & 1]), (uint32_t)((it + 1) >> 1) & 1u, wait_limit);
+  }
   const bool good = !__syncthreads_or(!ok) && !aborted;
   if (!good && t == 0) cpd_set_status(status, CPD_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -271,8 +288,27 @@ size_t cpd_gram_tc_smem(int Rp) {
   const int M3 = 3 * Rp, MT = (M3 + 127) / 128;
   const size_t ops = 2 * (size_t)MT * 128 * GT_TK * 2;
   const size_t e = (size_t)M3 * Rp * sizeof(float);
-  return ops > e ? ops : e;
+  return (ops > e ? ops : e) + 2 * (size_t)GT_TK * Rp * sizeof(float);   // + the two raw TMA tiles
 }
+
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+}  // namespace
 
 // Partial Grams of U (rows scaled by 1 / sigma into Uout when do_scale) into
 // h->Gpart, one per CTA; returns the number of partials in *nblk.
@@ -293,8 +329,21 @@ cpd_status cpd_gram_tc_launch(cpd_ctx* h, const float* Uin, float* Uout, int64_t
   const int per_sm = std::max(1, std::min(4, 512 / ncols));
   const int grid = std::min(h->num_sms * per_sm, h->gram_blocks);
   const long long limit = h->dbg_gram_wait > 0 ? h->dbg_gram_wait : GT_WAIT_CYCLES;
-  gram_tc_kernel<<<grid, GT_THREADS, shm, h->stream>>>(Uin, Uout, I, h->R, h->Rp, sigma, do_scale, h->Gpart, h->status,
-                                                       limit, h->dbg_gram_no_mma ? 0 : 1);
+  // 2D tensor map over U (Rp floats a row, 16-byte aligned rows: Rp is a
+  // multiple of 4), boxes of GT_TK rows x Rp, rows past I read as zeros
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cpd_fail(h, CPD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  CUtensorMap tmap;
+  const cuuint64_t gdim[2] = {(cuuint64_t)h->Rp, (cuuint64_t)std::max<int64_t>(I, 1)};
+  const cuuint64_t gstride[1] = {(cuuint64_t)h->Rp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)h->Rp, (cuuint32_t)GT_TK};
+  const cuuint32_t estride[2] = {1, 1};
+  const CUresult er = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Uin), gdim, gstride, box,
+                          estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (er != CUDA_SUCCESS) return cpd_fail(h, CPD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  gram_tc_kernel<<<grid, GT_THREADS, shm, h->stream>>>(tmap, Uin, Uout, I, h->R, h->Rp, sigma, do_scale, h->Gpart,
+                                                       h->status, limit, h->dbg_gram_no_mma ? 0 : 1);
   CPD_LAUNCH(h, "gram_tc");
   *nblk = grid;
   return CPD_OK;

@@ -5,10 +5,12 @@ configuration the bench times, after one captured ALS round:
 
 * all 131,072 CP-ARLS-LEV draws of a mode update equal the FP64 oracle's
   inverse-CDF draws from the same factors, ties excepted: a draw within
-  max(1e-12, 8 cond(G_k) 2^-53) C_k of a bin boundary (the factor Grams of
-  this Zipf(1.3) tensor grow ill-conditioned, and a float64 Gram fixes G_k^+
-  and the leverage scores only to ~cond(G_k) 2^-53); probabilities agree to
-  64 cond_max^2 2^-53 relative (a quadratic form in G_k^+ can lose cond^2);
+  min(1e-6, max(1e-12, 8 cond(G_k) 2^-53)) C_k of a bin boundary, cond over
+  the eigenvalues the pseudo-inverse keeps (the factor Grams of this
+  Zipf(1.3) tensor grow ill-conditioned, and a float64 Gram fixes G_k^+ and
+  the leverage scores only to ~cond(G_k) 2^-53); probabilities agree to
+  min(1e-6, 64 cond_max^2 2^-53) relative (a quadratic form in G_k^+ can
+  lose cond^2);
 * the downsampled MTTKRP of those draws equals the oracle's on 512 random
   output rows (their nonzeros picked out of the device COO), 1e-5 relative;
 * the solve and renormalisation equal the oracle's on those rows.
@@ -48,7 +50,8 @@ def test_billion_scale_mode_update_matches_oracle():
     ok = ~mism
     perr = np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok])
     print("probability max rel err %.2e" % perr)
-    assert perr < max(1e-10, 64 * max(conds) ** 2 * 2.0 ** -53)
+    assert perr < min(1e-6, max(1e-10, 64 * max(conds) ** 2 * 2.0 ** -53))
+    assert near.sum() < J // 100                  # the window is not vacuous
     w = 1.0 / (J * gp)
     Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, gi, w)
     rows = np.sort(np.random.default_rng(5).choice(dims[mode], size=512, replace=False))

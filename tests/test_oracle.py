@@ -457,3 +457,9 @@ def test_arls_tie_window_follows_gram_conditioning():
     drift = np.max(np.abs(np.cumsum(ell2) - st["cdf"])) / st["C"]
     assert drift > 1e-12                               # the fixed floor alone would not cover it
     assert drift <= oc.arls_tie_tolerance(st)
+    # a singular Gram: the condition number is taken over the eigenvalues the
+    # pseudo-inverse keeps, and the window stays finite (capped)
+    sing = np.hstack([good[:, :3], good[:, :1]])
+    st2 = oc.arls_build(sing)
+    assert np.isfinite(oc.gram_condition(st2["G"]))
+    assert oc.arls_tie_tolerance(st2) <= 1e-6
