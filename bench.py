@@ -425,8 +425,8 @@ def algorithmic(phase, w, stats):
         # R(R+1)/2 per row, as float32 lane operations
         return "alu", stats["I_mean"] * R * (R + 1) / 2 * DF64_TERM_OPS
     if phase == "solve":
-        # Y (G+_hi + G+_lo): 2 R^2 FMAs a row
-        return "alu", stats["I_mean"] * 2 * R * R
+        # Y G+ with G+ rounded to float32: R^2 FMAs a row
+        return "alu", stats["I_mean"] * R * R
     if phase == "exact":
         # every nonzero: N indices + value, N - 1 factor rows, one output row update
         nnz = w["nnz"]

@@ -72,9 +72,13 @@ typedef struct {
   uint64_t seed;           /* Philox4x64-10 key word 0 for all draws */
   int32_t leaf_rows;       /* STS-CP rows per tree leaf F; 0 means F = R */
   int32_t input_on_host;   /* 1: idx, vals, init_factors of cpd_create are host memory */
-  int64_t nnz_sel_capacity; /* deterministic mode only: most selected nonzeros one
+  int64_t nnz_sel_capacity; /* deterministic mode: most selected nonzeros one
                               downsampled MTTKRP may gather (its sorted work list is
-                              sized from it); 0 = nnz.  More latches CPD_ERR_CAPACITY */
+                              sized from it); 0 = nnz.  More latches CPD_ERR_CAPACITY.
+                              Otherwise: length of the row-bucketed work list used for
+                              modes whose I_n x R output exceeds 64 MB; 0 = min(nnz,
+                              2^27).  Selected nonzeros past it are processed
+                              unbucketed (same result, no error) */
   int64_t reserved_i64[3];
   int32_t sketched_gram;   /* 0: solve with G = *_{k!=n} U_k^T U_k (Eq. 5, Sec. 4);
                               1: with the Gram of the sampled rows, sum_j w_j h_j h_j^T,

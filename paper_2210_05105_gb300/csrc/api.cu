@@ -248,6 +248,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   }
   if (h->opt.method == CPD_STS_CP && (s = cpd_sts_alloc(h)) != CPD_OK) return s;
   if (h->opt.deterministic && (s = cpd_det_alloc(h)) != CPD_OK) return s;
+  if ((s = cpd_rowsort_alloc(h)) != CPD_OK) return s;
   if ((s = cpd_dense_init(h)) != CPD_OK) return s;
   if ((s = cpd_sample_init(h)) != CPD_OK) return s;
 

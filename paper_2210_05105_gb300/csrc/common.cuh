@@ -38,6 +38,7 @@ struct ModeLayout {
   int32_t* hot_rows = nullptr;
   int n_hot = 0;
   uint32_t* row_code = nullptr;   // I_n: CPD_HOT_BIT | slot for hot rows, else the row's nonzero count
+  bool row_sorted = false;        // the sampled SpMM sorts its nonzeros by output row (Y larger than L2)
 };
 #define CPD_HOT_BIT 0x80000000u
 constexpr int CPD_HOT_MIN_COUNT = 256;   // a row with fewer nonzeros stays in the global path
@@ -126,6 +127,13 @@ struct cpd_ctx {
   unsigned long long host_sweep = 0;
 
   std::vector<void*> allocs;
+
+  // row-sorted sampled SpMM (R > 64, modes whose output Y exceeds 96 MB)
+  int64_t rs_cap = 0;                  // selected nonzeros the sorted lists hold (multiple of 32)
+  uint32_t* rs_cnt = nullptr;          // Imax + 1: per-row counts, counted down again by the scatter
+  uint32_t* rs_off = nullptr;          // Imax + 1: row offsets (exclusive scan; total last)
+  uint32_t* rs_bsum = nullptr;         // scan scratch
+  uint4* rs_rec = nullptr;             // 2 rs_cap: 32-byte records (row, scale, column), sorted by row
 
   // deterministic downsampled MTTKRP (options.deterministic): sorted work
   // lists instead of floating-point atomics
@@ -330,6 +338,18 @@ __device__ __forceinline__ void df_dot_step(float& sh, float& sl, float ah, floa
   sl = __fadd_rn(sl, __fadd_rn(e, __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pe))));
 }
 
+// (sh, sl) += (xh, xl) * u for a float32 u: the Dot2 step with one
+// double-float operand (exact leading product xh u, TwoSum into sh, the
+// rounding errors and xl u gathered in sl)
+__device__ __forceinline__ void df_dot_step_f(float& sh, float& sl, float xh, float xl, float u) {
+  const float p = __fmul_rn(xh, u);
+  const float pe = __fmaf_rn(xh, u, -p);
+  float s, e;
+  df_two_sum(sh, p, s, e);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, __fmaf_rn(xl, u, pe)));
+}
+
 #define CPD_STREAM_ARLS 0ull
 #define CPD_STREAM_STS 1ull
 #define CPD_STREAM_INIT 2ull
@@ -374,6 +394,9 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
 cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y);
 // scan.cu
 cpd_status cpd_scan_u32(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);
+int64_t cpd_scan_u32_scratch(int64_t n);
+cpd_status cpd_scan_u32_buf(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
+                            uint32_t* bsum, cudaStream_t st);
 cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t n, int bits,
                               unsigned long long* keys_tmp, uint32_t* vals_tmp);
 cpd_status cpd_radix_sort_u64_dev(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t cap,
@@ -381,4 +404,5 @@ cpd_status cpd_radix_sort_u64_dev(cpd_ctx* h, unsigned long long* keys, uint32_t
                                   uint32_t* counts, unsigned long long** out_k, uint32_t** out_v);
 // det.cu (options.deterministic)
 cpd_status cpd_det_alloc(cpd_ctx* h);
+cpd_status cpd_rowsort_alloc(cpd_ctx* h);
 cpd_status cpd_det_mttkrp(cpd_ctx* h, int mode, const double* w, int64_t J, float* Y, int64_t* out_nnz_sel);

@@ -190,15 +190,20 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
 // 4 x 4 block bi of the Gram's upper block triangle (columns 4 a0 .. + 3 by
 // 4 b0 .. + 3) for the rows of row group rg.  Per row it reads two float4 of
 // the row-major tile and adds 16 exact float32 products into 16 independent
-// double-float chains; every GB_FLUSH tiles the chains are added into
-// float64 accumulators, so each df64 chain spans at most GB_FLUSH * TR / nrg
+// double-float chains; every GB_FLUSH tiles of GB_TR rows the chains are
+// added into float64 accumulators, so each df64 chain spans at most 1,024 / nrg
 // rows (error ~ that many 2^-48 of the sum of |terms|; the float64 adds run at
-// 1/64 of the float32 rate, so they are kept rare).  Each (block, row
-// group) writes its own float64 partial Gram (gram_reduce_kernel sums them in
-// a fixed order).
-constexpr int GB_FLUSH = 16;
+// 1/64 of the float32 rate, so they are kept rare).  Tiles of 128 rows halve
+// the share of the tile loads' latency left uncovered between barriers.  Each
+// (block, row group) writes its own float64 partial Gram (gram_reduce_kernel
+// sums them in a fixed order).
+#ifndef CPD_GB_MINB
+#define CPD_GB_MINB 2            // resident blocks per SM the register budget is sized for
+#endif
+constexpr int GB_TR = 128;
+constexpr int GB_FLUSH = 1024 / GB_TR;
 constexpr int GB_MAXT = 416;   // threads: one row group of nblk <= 406 blocks (R <= 112), 16 chains each
-__global__ void __launch_bounds__(GB_MAXT, 2) gram_blk_kernel(
+__global__ void __launch_bounds__(GB_MAXT, CPD_GB_MINB) gram_blk_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int nrg) {
   extern __shared__ float4 gbs4[];
@@ -231,12 +236,12 @@ __global__ void __launch_bounds__(GB_MAXT, 2) gram_blk_kernel(
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) { ah[i][j] = 0.0f; al[i][j] = 0.0f; acc64[(4 * i + j) * blockDim.x + t] = 0.0; }
-  const int64_t ntiles = cpd_ceil_div(I, TR);
+  const int64_t ntiles = cpd_ceil_div(I, GB_TR);
   int nt = 0;
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
-    const int64_t r0 = tl * TR;
+    const int64_t r0 = tl * GB_TR;
     __syncthreads();                             // previous tile consumed
-    for (int e = t; e < TR * Rp; e += blockDim.x) {
+    for (int e = t; e < GB_TR * Rp; e += blockDim.x) {
       const int rr = e / Rp, c = e % Rp;
       const int64_t i = r0 + rr;
       float v = 0.0f;
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(GB_MAXT, 2) gram_blk_kernel(
     __syncthreads();
     if (active) {
 #pragma unroll 1
-      for (int rr = rg; rr < TR; rr += nrg) {
+      for (int rr = rg; rr < GB_TR; rr += nrg) {
         const float4 x = *reinterpret_cast<const float4*>(tile + rr * Rp + a0);
         const float4 y = *reinterpret_cast<const float4*>(tile + rr * Rp + b0);
         const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
@@ -500,7 +505,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     const int i = e / R, j = e % R;
     const double p = 0.5 * (df_value(Xh[e], Xl[e]) + df_value(Xh[j * R + i], Xl[j * R + i]));
     jb.out_pinv[e] = p;
-    if (jb.out_split) {               // the solve's float32 hi + lo copy
+    if (jb.out_split) {               // the solve's float32 copy, and its float32 remainder
       const float hi = (float)p;
       jb.out_split[e] = hi;
       jb.out_split[RR + e] = (float)(p - (double)hi);
@@ -667,10 +672,12 @@ __global__ void __launch_bounds__(PINV_THREADS) pinv_kernel(PinvJobs jobs, int R
   }
 }
 
-// ---- solve: Uw = Y (P_hi + P_lo), float32 with the float64 G^+ split ----
+// ---- solve: Uw = Y P, P = G^+ rounded to float32 ---------------------------
 // Four threads per row, each owning a quarter of the RB (>= Rp) columns;
-// the row of Y in registers, P_hi / P_lo in shared memory read as 16-byte
-// vectors (one load feeds four FMAs per thread).  Column sums of squares:
+// the row of Y in registers, P in shared memory read as 16-byte vectors (one
+// load feeds four FMAs per thread).  o = fma(y_a, P[a][c], o), a = 0..R-1: the
+// float32 accumulation bounds the error, so G^+'s float32 remainder is not
+// carried.  Column sums of squares:
 // shuffles over the 8 rows a warp holds, then per-warp shared partials and a
 // fixed-order sum per block.
 template <int RB>
@@ -680,14 +687,12 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
   constexpr int CPT = RB / 4;          // columns per thread
   extern __shared__ float4 sm4[];
   float* Phi = reinterpret_cast<float*>(sm4);   // R x RB, zero past R
-  float* Plo = Phi + R * RB;
   __shared__ double wsq[DTHREADS / 32][CPD_MAX_RANK];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int q = t & 3, rl = t >> 2;
-  for (int e = t; e < R * RB; e += DTHREADS) {     // G^+ as float32 hi + lo (split by pinv_kernel)
+  for (int e = t; e < R * RB; e += DTHREADS) {     // G^+ rounded to float32 (by pinv_kernel)
     const int a = e / RB, c = e % RB;
     Phi[e] = c < R ? P2[a * R + c] : 0.0f;
-    Plo[e] = c < R ? P2[R * R + a * R + c] : 0.0f;
   }
   for (int c = lane; c < CPD_MAX_RANK; c += 32) wsq[wid][c] = 0.0;
   __syncthreads();
@@ -713,14 +718,13 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
       if (a < R) {
         const float ya = y[a];
         const float4* ph = reinterpret_cast<const float4*>(Phi + a * RB + c0);
-        const float4* pl = reinterpret_cast<const float4*>(Plo + a * RB + c0);
 #pragma unroll
         for (int v = 0; v < CPT / 4; ++v) {
-          const float4 h4 = ph[v], l4 = pl[v];
-          out[4 * v] = fmaf(ya, h4.x, fmaf(ya, l4.x, out[4 * v]));
-          out[4 * v + 1] = fmaf(ya, h4.y, fmaf(ya, l4.y, out[4 * v + 1]));
-          out[4 * v + 2] = fmaf(ya, h4.z, fmaf(ya, l4.z, out[4 * v + 2]));
-          out[4 * v + 3] = fmaf(ya, h4.w, fmaf(ya, l4.w, out[4 * v + 3]));
+          const float4 h4 = ph[v];
+          out[4 * v] = fmaf(ya, h4.x, out[4 * v]);
+          out[4 * v + 1] = fmaf(ya, h4.y, out[4 * v + 1]);
+          out[4 * v + 2] = fmaf(ya, h4.z, out[4 * v + 2]);
+          out[4 * v + 3] = fmaf(ya, h4.w, out[4 * v + 3]);
         }
       }
     }
@@ -752,12 +756,12 @@ __global__ void __launch_bounds__(DTHREADS) solve_kernel(
 }
 
 // ---- solve for R <= 32: one output column per lane ------------------------
-// Lane c of every warp owns output column c and holds column c of P_hi and
-// P_lo in registers.  The block stages SOLVE_TR rows of Y in shared memory
+// Lane c of every warp owns output column c and holds column c of P (G^+ in
+// float32) in registers.  The block stages SOLVE_TR rows of Y in shared memory
 // (the next tile is loaded into registers while the current one is used);
 // warp w takes rows w, w + 8, ... of the tile, two at a time, reading each
 // row as 16-byte broadcasts.  Every output sums its terms in the same order
-// as solve_kernel: o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
+// as solve_kernel: o = fma(y_a, P[a][c], o), a = 0..R-1.
 constexpr int SOLVE_TR = 64;
 __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
     const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R, int Rp,
@@ -766,13 +770,9 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
   __shared__ float4 ys4[SOLVE_TR * RB / 4];       // tile row r at r * RB / 4; columns >= Rp stay zero
   __shared__ float wsq[DTHREADS / 32][32];
   const int t = threadIdx.x, c = t & 31, wid = t >> 5;
-  float ph[RB], pl[RB];
+  float ph[RB];
 #pragma unroll
-  for (int a = 0; a < RB; ++a) {
-    const bool in = a < R && c < R;
-    ph[a] = in ? P2[a * R + c] : 0.0f;
-    pl[a] = in ? P2[R * R + a * R + c] : 0.0f;
-  }
+  for (int a = 0; a < RB; ++a) ph[a] = (a < R && c < R) ? P2[a * R + c] : 0.0f;
   const int C4 = Rp / 4;                          // float4 per row of Y (Rp <= 32)
   const int nv = SOLVE_TR * C4;                   // float4 per tile (<= 512 = 2 per thread)
   for (int e = t; e < SOLVE_TR * RB / 4; e += DTHREADS) ys4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -812,14 +812,14 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
 #pragma unroll
       for (int v = 0; v < RB / 4; ++v) {
         const float4 a0 = y0[v], a1 = y1[v];
-        o0 = fmaf(a0.x, ph[4 * v], fmaf(a0.x, pl[4 * v], o0));
-        o1 = fmaf(a1.x, ph[4 * v], fmaf(a1.x, pl[4 * v], o1));
-        o0 = fmaf(a0.y, ph[4 * v + 1], fmaf(a0.y, pl[4 * v + 1], o0));
-        o1 = fmaf(a1.y, ph[4 * v + 1], fmaf(a1.y, pl[4 * v + 1], o1));
-        o0 = fmaf(a0.z, ph[4 * v + 2], fmaf(a0.z, pl[4 * v + 2], o0));
-        o1 = fmaf(a1.z, ph[4 * v + 2], fmaf(a1.z, pl[4 * v + 2], o1));
-        o0 = fmaf(a0.w, ph[4 * v + 3], fmaf(a0.w, pl[4 * v + 3], o0));
-        o1 = fmaf(a1.w, ph[4 * v + 3], fmaf(a1.w, pl[4 * v + 3], o1));
+        o0 = fmaf(a0.x, ph[4 * v], o0);
+        o1 = fmaf(a1.x, ph[4 * v], o1);
+        o0 = fmaf(a0.y, ph[4 * v + 1], o0);
+        o1 = fmaf(a1.y, ph[4 * v + 1], o1);
+        o0 = fmaf(a0.z, ph[4 * v + 2], o0);
+        o1 = fmaf(a1.z, ph[4 * v + 2], o1);
+        o0 = fmaf(a0.w, ph[4 * v + 3], o0);
+        o1 = fmaf(a1.w, ph[4 * v + 3], o1);
       }
       const int64_t i0 = r0 + rr, i1 = r0 + rr + 8;
       if (i0 < I) {
@@ -842,32 +842,32 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
   }
 }
 
-// ---- solve for 32 < R <= 128: register-tiled Y (P_hi + P_lo) --------------
+// ---- solve for 32 < R <= 128: register-tiled Y P ------------------------------
 // A block of 16 TY threads (TY x 16) computes tiles of 8 TY rows x NB columns
 // (NB = 64 or 128 >= Rp): thread (ty, tx) owns rows 8 ty .. 8 ty + 7 and
 // columns TC tx .. TC tx + TC - 1 (TC = NB / 16), 8 TC accumulators in
-// registers.  G^+ (hi and lo, R x NB, zero past R) stays in shared memory for
-// the whole grid-stride loop; each tile of Y is staged transposed (Rp x tile
-// rows, consecutive lanes loading consecutive rows, so the transposing stores
-// do not conflict).  Per k the thread reads 8 values of Y and TC of each half
-// of G^+ as 16-byte vectors and issues 16 TC FMAs.  Every output adds its terms in the order of
-// solve_kernel: o = fma(y_a, P_hi[a][c], fma(y_a, P_lo[a][c], o)), a = 0..R-1.
+// registers.  P = G^+ rounded to float32 (R x NB, zero past R) stays in shared
+// memory for the whole grid-stride loop; each tile of Y is staged transposed
+// (Rp x tile rows, consecutive lanes loading consecutive rows, so the
+// transposing stores do not conflict).  Per k the thread reads 8 values of Y
+// and TC of P as 16-byte vectors and issues 8 TC FMAs: o = fma(y_a, P[a][c],
+// o), a = 0..R-1.  The float32 accumulation bounds the error (about 2^-24
+// sum_a |y_a P_ac| per output); carrying G^+'s float32 remainder as a second
+// FMA per term did not reduce it measurably, so it is left out here.
 template <int NB, int TY>
-__global__ void __launch_bounds__(16 * TY, 1) solve_tile_kernel(
+__global__ void __launch_bounds__(16 * TY, 2) solve_tile_kernel(
     const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R, int Rp,
     double* __restrict__ colpart) {
   constexpr int TC = NB / 16;
   constexpr int TM = 8 * TY, YS = TM + 4, NT = 16 * TY;
   extern __shared__ float4 sm4[];
   float* Ph = reinterpret_cast<float*>(sm4);     // R x NB
-  float* Pl = Ph + R * NB;                       // R x NB
-  float* Ys = Pl + R * NB;                       // Rp x YS (transposed tile; rows >= R hold Y's zero padding)
+  float* Ys = Ph + R * NB;                       // Rp x YS (transposed tile; rows >= R hold Y's zero padding)
   __shared__ float wsq[TY][NB];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
   for (int e = t; e < R * NB; e += NT) {
     const int a = e / NB, c = e % NB;
     Ph[e] = c < R ? P2[a * R + c] : 0.0f;
-    Pl[e] = c < R ? P2[R * R + a * R + c] : 0.0f;
   }
   float csq[TC];
 #pragma unroll
@@ -896,18 +896,16 @@ __global__ void __launch_bounds__(16 * TY, 1) solve_tile_kernel(
       const float4 y0 = *reinterpret_cast<const float4*>(Ys + a * YS + 8 * ty);
       const float4 y1 = *reinterpret_cast<const float4*>(Ys + a * YS + 8 * ty + 4);
       const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-      float ph[TC], pl[TC];
+      float ph[TC];
 #pragma unroll
       for (int v = 0; v < TC / 4; ++v) {
         const float4 h4 = *reinterpret_cast<const float4*>(Ph + a * NB + TC * tx + 4 * v);
-        const float4 l4 = *reinterpret_cast<const float4*>(Pl + a * NB + TC * tx + 4 * v);
         ph[4 * v] = h4.x; ph[4 * v + 1] = h4.y; ph[4 * v + 2] = h4.z; ph[4 * v + 3] = h4.w;
-        pl[4 * v] = l4.x; pl[4 * v + 1] = l4.y; pl[4 * v + 2] = l4.z; pl[4 * v + 3] = l4.w;
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(yv[i], ph[j], fmaf(yv[i], pl[j], acc[i][j]));
+        for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(yv[i], ph[j], acc[i][j]);
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -938,7 +936,7 @@ __global__ void __launch_bounds__(16 * TY, 1) solve_tile_kernel(
 }
 
 static size_t solve_tile_smem(int R, int NB, int TY) {
-  return ((size_t)2 * R * NB + (size_t)cpd_pad4(R) * (8 * TY + 4)) * sizeof(float);
+  return ((size_t)R * NB + (size_t)cpd_pad4(R) * (8 * TY + 4)) * sizeof(float);
 }
 // 256-row tiles of 512 threads were measured slower than 128-row tiles of
 // 256 threads at R = 100 (22.6 against 20.0 ms a round at the billion-scale
@@ -976,17 +974,22 @@ __global__ void fit_inner_kernel(const int32_t* __restrict__ idx, const float* _
     for (int k = 0; k < CPD_MAX_MODES; ++k) ii[k] = (k < a.N && e < nnz) ? idx[(int64_t)k * nnz + e] : 0;
     int cnt = (int)(nnz - c0 < 32 ? nnz - c0 : 32);
     float part32 = 0.0f;
+    // (unrolled so that the factor-row gathers of several nonzeros are in
+    // flight at once; the additions keep their order)
+#pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
-      float vj = __shfl_sync(CPD_FULL, v, j);
+      const float vj = __shfl_sync(CPD_FULL, v, j);
+      int32_t ij[CPD_MAX_MODES];
+#pragma unroll
+      for (int k = 0; k < CPD_MAX_MODES; ++k) ij[k] = __shfl_sync(CPD_FULL, ii[k], j);
 #pragma unroll
       for (int q = 0; q < CPD_MAX_RANK / 32; ++q) {
         int r = lane + 32 * q;
         if (32 * q < a.R) {
           float m = sg[q];
-          for (int k = 0; k < a.N; ++k) {
-            int ik = __shfl_sync(CPD_FULL, ii[k], j);
-            m *= (r < a.R) ? a.U[k][(int64_t)ik * a.Rp + r] : 0.0f;
-          }
+#pragma unroll
+          for (int k = 0; k < CPD_MAX_MODES; ++k)
+            if (k < a.N) m *= (r < a.R) ? a.U[k][(int64_t)ij[k] * a.Rp + r] : 0.0f;
           part32 = fmaf(vj, m, part32);
         }
       }
@@ -1041,8 +1044,8 @@ static cpd_status gram_from(cpd_ctx* h, const float* Uin, float* Uout, int64_t I
     const int nb4 = h->Rp / 4, nblk = nb4 * (nb4 + 1) / 2;
     const int nrg = 1;
     if (nblk > GB_MAXT) return cpd_fail(h, CPD_ERR_INVALID_ARG, "Gram block triangle exceeds the kernel's block size");
-    const int grid = std::max(1, std::min(2 * h->num_sms, h->gram_blocks / nrg));   // two CTAs per SM
-    const size_t gshm = (size_t)16 * nblk * nrg * sizeof(double) + (size_t)TR * h->Rp * sizeof(float);
+    const int grid = std::max(1, std::min(CPD_GB_MINB * h->num_sms, h->gram_blocks / nrg));
+    const size_t gshm = (size_t)16 * nblk * nrg * sizeof(double) + (size_t)GB_TR * h->Rp * sizeof(float);
     gram_blk_kernel<<<grid, nblk * nrg, gshm, h->stream>>>(Uin, Uout, I, R, h->Rp, sigma, do_scale, h->Gpart, nrg);
     CPD_LAUNCH(h, "gram_blk");
     gram_reduce_kernel<<<std::max(1, (npairs + 7) / 8), 256, 0, h->stream>>>(h->Gpart, grid * nrg, R, G);
@@ -1137,7 +1140,7 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
   {
     PhaseTimer pt(h, CPD_PHASE_SOLVE);
     const int rb = solve_rb(R);
-    size_t shm = (size_t)(2 * R * rb) * sizeof(float);
+    size_t shm = (size_t)(R * rb) * sizeof(float);
     int nblk = h->gram_blocks;                  // column partials summed by sigma_kernel
     if (rb == 32) {
       // two resident blocks per SM (118 registers a thread)
@@ -1146,10 +1149,19 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     } else if (rb == 16)
       solve_kernel<16><<<h->gram_blocks, DTHREADS, shm, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     else {
-      // one block per SM (the tile and G^+ fill most of its shared memory)
+      // as many blocks as are resident together (two per SM up to R ~ 100,
+      // where the tile and G^+ take 104 KB of shared memory a block)
       const int nb = rb == 64 ? 64 : 128, ty = solve_tile_ty(R, nb);
-      nblk = (int)std::min<int64_t>(h->num_sms, std::max<int64_t>(cpd_ceil_div(I, 8 * ty), 1));
       const size_t sh = solve_tile_smem(R, nb, ty);
+      int occ = 1;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &occ, nb == 64 ? (const void*)solve_tile_kernel<64, 16> : (const void*)solve_tile_kernel<128, 16>, 256,
+              sh) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+      }
+      nblk = (int)std::min<int64_t>(std::min<int64_t>((int64_t)occ * h->num_sms, h->gram_blocks),
+                                    std::max<int64_t>(cpd_ceil_div(I, 8 * ty), 1));
       if (nb == 64)
         solve_tile_kernel<64, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
       else
@@ -1189,13 +1201,13 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
   const int R = h->R;
   size_t s1 = (size_t)TRP * R * sizeof(float);
   size_t s2 = pinv_smem(R);
-  size_t s3 = (size_t)(2 * R * solve_rb(R)) * sizeof(float);
+  size_t s3 = (size_t)(R * solve_rb(R)) * sizeof(float);
   const std::pair<const void*, size_t> attrs[] = {
       {(const void*)normalize_gram_kernel<1>, s1}, {(const void*)normalize_gram_kernel<3>, s1},
       {(const void*)normalize_gram_kernel<9>, s1}, {(const void*)normalize_gram_kernel<33>, s1},
       {(const void*)pinv_kernel, s2},              {(const void*)solve_kernel<16>, s3},
       {(const void*)solve_kernel<32>, s3},
-      {(const void*)gram_blk_kernel, (size_t)16 * GB_MAXT * sizeof(double) + (size_t)TR * CPD_MAX_RANK * sizeof(float)},
+      {(const void*)gram_blk_kernel, (size_t)16 * GB_MAXT * sizeof(double) + (size_t)GB_TR * CPD_MAX_RANK * sizeof(float)},
       {(const void*)solve_tile_kernel<64, 16>, solve_tile_smem(std::min(R, 64), 64, 16)},
       {(const void*)solve_tile_kernel<128, 16>, solve_tile_smem(R, 128, 16)}};
   for (const auto& a : attrs) {

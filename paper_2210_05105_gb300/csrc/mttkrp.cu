@@ -172,12 +172,14 @@ __device__ __forceinline__ void spmm_step(const MArgs& a, int Rp, int C, int q, 
   if (r & CPD_HOT_BIT) {
     const uint32_t slot = r & ~CPD_HOT_BIT;
     if ((int)slot < Hs) {
-      float* acc = hot_acc + (size_t)slot * (Rp + 1) + 4 * q;
-      atomicAdd(acc + 0, sj * hv.x);
-      atomicAdd(acc + 1, sj * hv.y);
-      atomicAdd(acc + 2, sj * hv.z);
-      atomicAdd(acc + 3, sj * hv.w);
-      reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * (Rp + 1))[slot] = 1u;
+      // column 4 q + c of the slot's row lives at c C + q: the C lanes of a
+      // group add into consecutive words (distinct banks)
+      float* acc = hot_acc + (size_t)slot * (Rp + 1) + q;
+      atomicAdd(acc, sj * hv.x);
+      atomicAdd(acc + C, sj * hv.y);
+      atomicAdd(acc + 2 * C, sj * hv.z);
+      atomicAdd(acc + 3 * C, sj * hv.w);
+      if (q == 0) reinterpret_cast<unsigned int*>(hot_acc + (size_t)Hs * (Rp + 1))[slot] = 1u;
       return;
     }
     r = (uint32_t)a.hot_rows[slot];
@@ -188,12 +190,232 @@ __device__ __forceinline__ void spmm_step(const MArgs& a, int Rp, int C, int q, 
                : "memory");
 }
 
-// RPT: the row stride Rp as a compile-time constant (lane-group shape and
-// address arithmetic fold), or 0 for a.Rp at run time.
+// Position p of the flat list of selected nonzeros (chunk c = p / 32 of a
+// warp, one position per lane) -> its row code, weight x value and distinct
+// column.  The 32 positions of a chunk meet at most 32 consecutive segments
+// starting at the one the probe recorded for the chunk; the window of their
+// offsets goes to the lanes, and each lane finds its own segment in the
+// window by shuffles.  All 32 lanes take part; positions >= total get
+// scale 0.
+__device__ __forceinline__ void locate_selected(const MArgs& a, uint32_t nu, uint32_t total, int64_t c, int lane,
+                                                uint32_t& row, float& scale, uint32_t& useg) {
+  const int64_t p = c * 32 + lane;
+  const uint32_t seg0 = a.chunk_seg[c];
+  const uint32_t wseg = seg0 + lane;
+  const uint32_t woff = wseg < nu ? a.uq_off[wseg] : 0xffffffffu;
+  uint32_t loc = 0;                      // last window slot with offset <= p
+#pragma unroll
+  for (int b = 16; b > 0; b >>= 1) {
+    const uint32_t o = __shfl_sync(CPD_FULL, woff, (int)(loc + b));
+    if (o <= (uint32_t)p) loc += b;
+  }
+  const uint32_t segoff = __shfl_sync(CPD_FULL, woff, (int)loc);
+  row = 0; useg = 0; scale = 0.0f;
+  if (p < total) {
+    useg = seg0 + loc;
+    // the entry's address does not wait for the dedup slot: the column's
+    // first entry was recorded by the probe
+    const uint32_t slot = a.uq_slot[useg];
+    const uint32_t e = a.uq_beg[useg] + ((uint32_t)p - segoff);
+    const uint2 en = a.ent[e];
+    row = en.x;
+    scale = a.dd_w[slot] * __uint_as_float(en.y);
+  }
+}
+
+// The cnt (<= 32) nonzeros held one per lane (row code, scale, column) of a
+// warp.  C lanes cover one row of Rp floats (C <= 32 since R <= 128) with
+// 16-byte vector reductions, so one warp instruction updates E = 32 / C
+// selected nonzeros at once.  Consecutive nonzeros of a lane group often
+// belong to the same drawn column, so its KRP row is kept in registers and
+// loaded again only when the column changes.
 template <int RPT>
-__global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel) {
-  // hot rows: one float row (stride Rp + 1, so rows start in different banks)
-  // per slot, and a touched flag per slot; flushed to Y once per block
+__device__ __forceinline__ void spmm_warp(const MArgs& a, int Rp, int C, int E, int sub, int q, int Hs,
+                                          float* __restrict__ hot_acc, float* __restrict__ Y, uint32_t row,
+                                          float scale, uint32_t useg, int cnt) {
+  uint32_t cu = 0xffffffffu;
+  float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (RPT && E * C == 32 && cnt == 32) {
+    // a full chunk and a lane-group shape that fills the warp: every step is
+    // valid (four steps unrolled at Rp >= 32, two at Rp = 16: more would
+    // spill at 32 registers)
+#pragma unroll (RPT >= 32 ? 4 : 2)
+    for (int j0 = 0; j0 < 32; j0 += E) {
+      const int jj = j0 + sub;
+      const uint32_t r = __shfl_sync(CPD_FULL, row, jj);
+      const float sj = __shfl_sync(CPD_FULL, scale, jj);
+      const uint32_t uj = __shfl_sync(CPD_FULL, useg, jj);
+      spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
+    }
+  } else {
+    for (int j0 = 0; j0 < cnt; j0 += E) {
+      const int jj = j0 + sub;
+      const int src = jj < 32 ? jj : 31;
+      const uint32_t r = __shfl_sync(CPD_FULL, row, src);
+      const float sj = __shfl_sync(CPD_FULL, scale, src);
+      const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
+      if (!(sub < E && jj < cnt)) continue;
+      spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
+    }
+  }
+}
+
+// Row-sorted SpMM, for outputs Y larger than L2 (R > 64).  There the vector
+// reductions of the flat-list SpMM miss L2 and read-modify-write DRAM
+// sectors; most cold rows take only a few selected nonzeros, so even the
+// zeros of a cleared Y come back from DRAM.  Instead the selected nonzeros
+// of the cold rows are counting-sorted by output row (count, scan, scatter of
+// one full 32-byte record each, so no DRAM sector is read back), and a flat
+// pass over the sorted list (warps take 32 consecutive positions, load
+// balanced) sums each run of one row in registers: a row whose nonzeros all
+// lie in one 32-position chunk is stored once, a row crossing a chunk
+// boundary gets one vector reduction per chunk into zeros that a streaming
+// pass stored beforehand (with the rows that have no sorted nonzeros), so Y
+// is written, not read, except for those rows.  The rows this launch keeps in
+// shared memory (the hot rows) stay out of the sort: the flat-list SpMM takes
+// them afterwards in column order (their KRP rows reused across a column's
+// run), together with every position past the sorted list's capacity.
+struct RowSort {
+  uint32_t* cnt;        // I: per-row counts (pass 0), counted down by pass 1
+  const uint32_t* off;  // I + 1: row offsets (off[I] = sorted positions)
+  uint4* rec;           // 2 cap: 32-byte records {row, scale bits, column, 0; 0, 0, 0, 0}, sorted
+  uint32_t cap;         // multiple of 32
+  int64_t I;
+};
+
+// PASS 0 counts the selected nonzeros of each cold row; PASS 1 places them
+// at off[row] + (count, decremented).  A warp a chunk of 32 positions
+// (positions < min(total, cap)); entries of rows with a shared-memory slot of
+// this launch (slot < Hs) are skipped.
+template <int PASS>
+__global__ void __launch_bounds__(256) rowsort_kernel(MArgs a, int Hs, RowSort rs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long pk = *reinterpret_cast<const unsigned long long*>(a.counters);
+  const uint32_t nu = min((uint32_t)(pk >> 32), a.uq_cap);
+  const uint32_t lim = min((uint32_t)(pk & 0xffffffffull), rs.cap);
+  const int64_t nchunks = ((int64_t)lim + 31) / 32;
+  for (int64_t c = warp; c < nchunks; c += nwarps) {
+    uint32_t code, useg;
+    float scale;
+    locate_selected(a, nu, lim, c, lane, code, scale, useg);
+    if (c * 32 + lane >= (int64_t)lim) continue;
+    uint32_t row = code;
+    if (code & CPD_HOT_BIT) {
+      const uint32_t slot = code & ~CPD_HOT_BIT;
+      if ((int)slot < Hs) continue;
+      row = (uint32_t)a.hot_rows[slot];
+    }
+    if (PASS == 0) {
+      atomicAdd(&rs.cnt[row], 1u);
+    } else {
+      const uint32_t at = rs.off[row] + atomicSub(&rs.cnt[row], 1u) - 1u;
+      uint4* r = rs.rec + 2 * (size_t)at;
+      r[0] = make_uint4(row, __float_as_uint(scale), useg, 0u);
+      r[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
+// Zeros for every row without sorted nonzeros and every row whose nonzeros
+// cross a 32-position chunk boundary (those take vector reductions); C lanes
+// a row.
+__global__ void __launch_bounds__(1024, 2) rowsort_zero_kernel(float* __restrict__ Y, int Rp, RowSort rs) {
+  const int lane = threadIdx.x & 31;
+  const int C = Rp / 4;
+  const int E = C >= 32 ? 1 : 32 / C;
+  const int sub = C >= 32 ? 0 : lane / C;
+  const int q = C >= 32 ? lane : lane % C;
+  if (sub >= E) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * E;
+  for (int64_t r = warp * E + sub; r < rs.I; r += ngroups) {
+    const uint32_t b = rs.off[r], e = rs.off[r + 1];
+    if (b == e || (b >> 5) != ((e - 1) >> 5))
+      reinterpret_cast<float4*>(Y + r * Rp)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+}
+
+// The sorted positions, 32 a warp (Rp > 64: one lane group of C <= 32 lanes
+// a warp).  RS_BATCH positions at a time have their KRP rows loaded before
+// they are summed; a run of one row ends in a store (row inside the chunk) or a
+// vector reduction (row crossing the chunk's first or last position).
+constexpr int RS_BATCH = 4;
+template <int RPT>
+__global__ void __launch_bounds__(512, 2) rowsort_flat_kernel(MArgs a, float* __restrict__ Y, RowSort rs) {
+  const int Rp = RPT ? RPT : a.Rp;
+  const int C = Rp / 4;
+  const int lane = threadIdx.x & 31;
+  const int q = lane;                       // lanes >= C take part in the shuffles only
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t lim = rs.off[rs.I];
+  const int64_t nchunks = ((int64_t)lim + 31) / 32;
+  const float4* H4 = reinterpret_cast<const float4*>(a.H);
+  for (int64_t c = warp; c < nchunks; c += nwarps) {
+    const int64_t p = c * 32 + lane;
+    const bool in = p < (int64_t)lim;
+    const uint4 rc = in ? rs.rec[2 * p] : make_uint4(0xffffffffu, 0u, 0u, 0u);
+    const uint32_t row = rc.x;
+    const float sc = __uint_as_float(rc.y);
+    const uint32_t col = rc.z;
+    const uint32_t prev = c > 0 ? rs.rec[2 * (c * 32 - 1)].x : 0xffffffffu;
+    const uint32_t next = c * 32 + 32 < (int64_t)lim ? rs.rec[2 * (c * 32 + 32)].x : 0xffffffffu;
+    const int cnt = (int)((int64_t)lim - c * 32 < 32 ? (int64_t)lim - c * 32 : 32);
+    uint32_t cur = __shfl_sync(CPD_FULL, row, 0);
+    bool first = true;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    auto flush = [&](bool span) {
+      if (q < C) {
+        float* yp = Y + (int64_t)cur * Rp + 4 * q;
+        if (span)
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc.x), "f"(acc.y),
+                       "f"(acc.z), "f"(acc.w)
+                       : "memory");
+        else
+          *reinterpret_cast<float4*>(yp) = acc;
+      }
+    };
+    for (int j0 = 0; j0 < cnt; j0 += RS_BATCH) {
+      uint32_t rj[RS_BATCH];
+      float sj[RS_BATCH];
+      float4 hv[RS_BATCH];
+#pragma unroll
+      for (int u = 0; u < RS_BATCH; ++u) {
+        const int jj = min(j0 + u, 31);
+        rj[u] = __shfl_sync(CPD_FULL, row, jj);
+        sj[u] = __shfl_sync(CPD_FULL, sc, jj);
+        const uint32_t cj = __shfl_sync(CPD_FULL, col, jj);
+        hv[u] = (j0 + u < cnt && q < C) ? H4[(int64_t)cj * C + q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < RS_BATCH; ++u) {
+        if (j0 + u < cnt) {
+          if (rj[u] != cur) {
+            flush(first && cur == prev);
+            first = false;
+            cur = rj[u];
+            acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
+          acc.x = fmaf(sj[u], hv[u].x, acc.x); acc.y = fmaf(sj[u], hv[u].y, acc.y);
+          acc.z = fmaf(sj[u], hv[u].z, acc.z); acc.w = fmaf(sj[u], hv[u].w, acc.w);
+        }
+      }
+    }
+    flush((first && cur == prev) || cur == next);
+  }
+}
+
+// RPT: the row stride Rp as a compile-time constant (lane-group shape and
+// address arithmetic fold), or 0 for a.Rp at run time.  hot_below: the
+// positions below 32 c_begin were row-sorted except the shared-memory rows'.
+template <int RPT>
+__global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restrict__ Y, int64_t* __restrict__ out_nnz_sel,
+                                                       int64_t c_begin, int hot_below) {
+  // hot rows: one float row (stride Rp + 1, so rows start in different banks;
+  // column 4 q + c at c Rp / 4 + q) per slot, and a touched flag per slot;
+  // flushed to Y once per block
   extern __shared__ float hot_acc[];
   const int Rp = RPT ? RPT : a.Rp;
   const int S = Rp + 1;
@@ -214,75 +436,35 @@ __global__ void __launch_bounds__(1024, 2) spmm_kernel(MArgs a, float* __restric
   const int E = C >= 32 ? 1 : 32 / C;     // nonzeros per warp instruction
   const int sub = C >= 32 ? 0 : lane / C; // which of the E nonzeros this lane serves
   const int q = C >= 32 ? lane : lane % C;
-  for (int64_t c = warp; c < nchunks; c += nwarps) {
-    const int64_t p = c * 32 + lane;
-    // The 32 positions of the chunk meet at most 32 consecutive segments
-    // starting at the one the probe recorded for the chunk; the window of
-    // their offsets goes to the lanes, and each lane locates its own segment
-    // in the window by shuffles.
-    const uint32_t seg0 = a.chunk_seg[c];
-    const uint32_t wseg = seg0 + lane;
-    const uint32_t woff = wseg < nu ? a.uq_off[wseg] : 0xffffffffu;
-    uint32_t loc = 0;                      // last window slot with offset <= p
-#pragma unroll
-    for (int b = 16; b > 0; b >>= 1) {
-      const uint32_t o = __shfl_sync(CPD_FULL, woff, (int)(loc + b));
-      if (o <= (uint32_t)p) loc += b;
+  // Below 32 c_begin (the row-sorted list's positions) only the entries of
+  // this launch's shared-memory rows are taken, moved to the front of the
+  // chunk in order by a ballot; from 32 c_begin on, every entry.
+  for (int64_t c = (hot_below ? 0 : c_begin) + warp; c < nchunks; c += nwarps) {
+    uint32_t row, useg;
+    float scale;
+    locate_selected(a, nu, total, c, lane, row, scale, useg);
+    int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
+    if (hot_below && c < c_begin) {
+      const bool keep = lane < cnt && (row & CPD_HOT_BIT) && (int)(row & ~CPD_HOT_BIT) < Hs;
+      const unsigned km = __ballot_sync(CPD_FULL, keep);
+      cnt = __popc(km);
+      if (cnt == 0) continue;
+      const int src = lane < cnt ? (int)__fns(km, 0, lane + 1) : 0;
+      row = __shfl_sync(CPD_FULL, row, src);
+      scale = __shfl_sync(CPD_FULL, scale, src);
+      useg = __shfl_sync(CPD_FULL, useg, src);
     }
-    const uint32_t segoff = __shfl_sync(CPD_FULL, woff, (int)loc);
-    uint32_t row = 0, useg = 0;
-    float scale = 0.0f;
-    if (p < total) {
-      useg = seg0 + loc;
-      // the entry's address does not wait for the dedup slot: the column's
-      // first entry was recorded by the probe
-      const uint32_t slot = a.uq_slot[useg];
-      const uint32_t e = a.uq_beg[useg] + ((uint32_t)p - segoff);
-      const uint2 en = a.ent[e];
-      row = en.x;
-      scale = a.dd_w[slot] * __uint_as_float(en.y);
-    }
-    const int cnt = (int)((int64_t)total - c * 32 < 32 ? (int64_t)total - c * 32 : 32);
-    // C lanes cover one row of Rp floats (C <= 32 since R <= 128) with
-    // 16-byte vector reductions, so one warp instruction updates E = 32 / C
-    // selected nonzeros at once.  Consecutive positions of a lane group
-    // mostly belong to the same drawn column, so its KRP row is kept in
-    // registers and loaded again only when the column changes.
-    uint32_t cu = 0xffffffffu;
-    float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (RPT && E * C == 32 && cnt == 32) {
-      // a full chunk and a lane-group shape that fills the warp: every step
-      // is valid (four steps unrolled at Rp >= 32, two at Rp = 16: more would
-      // spill at 32 registers)
-#pragma unroll (RPT >= 32 ? 4 : 2)
-      for (int j0 = 0; j0 < 32; j0 += E) {
-        const int jj = j0 + sub;
-        const uint32_t r = __shfl_sync(CPD_FULL, row, jj);
-        const float sj = __shfl_sync(CPD_FULL, scale, jj);
-        const uint32_t uj = __shfl_sync(CPD_FULL, useg, jj);
-        spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
-      }
-    } else {
-      for (int j0 = 0; j0 < cnt; j0 += E) {
-        const int jj = j0 + sub;
-        const int src = jj < 32 ? jj : 31;
-        const uint32_t r = __shfl_sync(CPD_FULL, row, src);
-        const float sj = __shfl_sync(CPD_FULL, scale, src);
-        const uint32_t uj = __shfl_sync(CPD_FULL, useg, src);
-        if (!(sub < E && jj < cnt)) continue;
-        spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
-      }
-    }
+    spmm_warp<RPT>(a, Rp, C, E, sub, q, Hs, hot_acc, Y, row, scale, useg, cnt);
   }
   // flush the block's hot rows that it touched
   __syncthreads();
   for (int i = threadIdx.x; i < Hs * C; i += blockDim.x) {
     const int slot = i / C, qq = i - slot * C;
     if (!touched[slot]) continue;
-    const float* acc = hot_acc + (size_t)slot * S + 4 * qq;
+    const float* acc = hot_acc + (size_t)slot * S + qq;
     float* yp = Y + (int64_t)a.hot_rows[slot] * Rp + 4 * qq;
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[1]), "f"(acc[2]),
-                 "f"(acc[3])
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[C]),
+                 "f"(acc[2 * C]), "f"(acc[3 * C])
                  : "memory");
   }
 }
@@ -349,12 +531,12 @@ __global__ void __launch_bounds__(512, 2) exact_kernel(MArgs a, const int32_t* _
       const uint32_t code = a.row_code ? a.row_code[row] : 0u;
       if ((code & CPD_HOT_BIT) && (int)(code & ~CPD_HOT_BIT) < Hs) {
         const uint32_t slot = code & ~CPD_HOT_BIT;
-        float* acc = hot_acc + (size_t)slot * S + 4 * q;
-        atomicAdd(acc + 0, hv.x);
-        atomicAdd(acc + 1, hv.y);
-        atomicAdd(acc + 2, hv.z);
-        atomicAdd(acc + 3, hv.w);
-        touched[slot] = 1u;
+        float* acc = hot_acc + (size_t)slot * S + q;   // column 4 q + c at c C + q
+        atomicAdd(acc, hv.x);
+        atomicAdd(acc + C, hv.y);
+        atomicAdd(acc + 2 * C, hv.z);
+        atomicAdd(acc + 3 * C, hv.w);
+        if (q == 0) touched[slot] = 1u;
       } else {
         float* yp = Y + (int64_t)row * a.Rp + 4 * q;
         asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(hv.x), "f"(hv.y), "f"(hv.z),
@@ -367,10 +549,10 @@ __global__ void __launch_bounds__(512, 2) exact_kernel(MArgs a, const int32_t* _
   for (int i = threadIdx.x; i < Hs * C; i += blockDim.x) {
     const int slot = i / C, qq = i - slot * C;
     if (!touched[slot]) continue;
-    const float* acc = hot_acc + (size_t)slot * S + 4 * qq;
+    const float* acc = hot_acc + (size_t)slot * S + qq;
     float* yp = Y + (int64_t)a.hot_rows[slot] * a.Rp + 4 * qq;
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[1]), "f"(acc[2]),
-                 "f"(acc[3])
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(yp), "f"(acc[0]), "f"(acc[C]),
+                 "f"(acc[2 * C]), "f"(acc[3 * C])
                  : "memory");
   }
 }
@@ -425,6 +607,31 @@ cpd_status cpd_spmm_init(cpd_ctx* h) {
   return s4 != CPD_OK ? s4 : cpd_smem_attr(h, (const void*)exact_kernel<CPD_MAX_MODES>, shm);
 }
 
+// Row-sorted SpMM for every mode whose output Y (I_n x Rp floats, Rp > 64)
+// exceeds 96 MB, three quarters of L2: per-row counts and offsets for the
+// largest such mode, and sorted lists of min(nnz, nnz_sel_capacity or 2^27)
+// selected nonzeros shared by the modes; selected nonzeros past them take the
+// flat-list path.
+cpd_status cpd_rowsort_alloc(cpd_ctx* h) {
+  if (h->opt.deterministic || h->nnz == 0 || h->Rp <= 64) return CPD_OK;
+  int64_t imax = 0;
+  for (int k = 0; k < h->N; ++k) {
+    h->mode[k].row_sorted = h->dims[k] * (int64_t)h->Rp * 4 > ((int64_t)96 << 20);
+    if (h->mode[k].row_sorted) imax = std::max(imax, h->dims[k]);
+  }
+  if (imax == 0) return CPD_OK;
+  int64_t cap = h->opt.nnz_sel_capacity > 0 ? h->opt.nnz_sel_capacity : ((int64_t)1 << 27);
+  cap = std::min<int64_t>(cap, h->nnz);
+  cap = std::min<int64_t>(cpd_ceil_div(cap, 32) * 32, (int64_t)0xffffffe0ll);
+  cpd_status s;
+  if ((s = cpd_alloc(h, &h->rs_cnt, (size_t)imax + 1)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->rs_off, (size_t)imax + 1)) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->rs_bsum, (size_t)cpd_scan_u32_scratch(imax))) != CPD_OK) return s;
+  if ((s = cpd_alloc(h, &h->rs_rec, (size_t)2 * cap)) != CPD_OK) return s;
+  h->rs_cap = cap;
+  return CPD_OK;
+}
+
 namespace {
 
 MArgs make_args(cpd_ctx* h, int mode) {
@@ -451,7 +658,9 @@ MArgs make_args(cpd_ctx* h, int mode) {
 // Y (I_mode x Rp, internal stride) := mat(T, mode) S^T S U_{!=mode}.
 // Y = 0 (rows of `mode`), dedup tables empty, counters 0, on stream st.
 cpd_status cpd_clear_launch(cpd_ctx* h, int mode, float* Y, cudaStream_t st) {
-  const int64_t ny4 = h->dims[mode] * (int64_t)h->Rp / 4;      // Rp is a multiple of 4
+  // (row-sorted modes: the SpMM stores every row of Y itself)
+  const bool sorted = h->rs_cap > 0 && h->mode[mode].row_sorted;
+  const int64_t ny4 = sorted ? 0 : h->dims[mode] * (int64_t)h->Rp / 4;      // Rp is a multiple of 4
   const int64_t nd4 = ((int64_t)h->dedup_mask + 1) / 4;          // 2J slots, a power of two >= 4
   clear_kernel<<<h->num_sms * 4, 256, 0, st>>>(reinterpret_cast<float4*>(Y), ny4,
                                                 reinterpret_cast<uint4*>(h->dd_tag),
@@ -490,12 +699,38 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
     a.hot_rows = h->mode[mode].hot_rows;
     const size_t shm = spmm_smem(cpd_spmm_threads(bps), a.n_hot, h->Rp);
     const dim3 grid(h->num_sms * bps), block(cpd_spmm_threads(bps));
+    RowSort rs;
+    memset(&rs, 0, sizeof(rs));
+    const bool sorted = h->rs_cap > 0 && h->mode[mode].row_sorted;
+    int64_t c_begin = 0;
+    if (sorted) {
+      const int64_t I = h->dims[mode];
+      rs.cnt = h->rs_cnt; rs.off = h->rs_off; rs.rec = h->rs_rec;
+      rs.cap = (uint32_t)h->rs_cap; rs.I = I;
+      CPD_CUDA(h, cudaMemsetAsync(h->rs_cnt, 0, (size_t)I * sizeof(uint32_t), st));
+      const int g = h->num_sms * 8;
+      rowsort_kernel<0><<<g, 256, 0, st>>>(a, a.n_hot, rs);
+      CPD_LAUNCH(h, "spmm row count");
+      const cpd_status ss = cpd_scan_u32_buf(h, h->rs_cnt, h->rs_off, I, h->rs_off + I, h->rs_bsum, st);
+      if (ss != CPD_OK) return ss;
+      rowsort_kernel<1><<<g, 256, 0, st>>>(a, a.n_hot, rs);
+      CPD_LAUNCH(h, "spmm row scatter");
+      rowsort_zero_kernel<<<h->num_sms * 2, 1024, 0, st>>>(Y, h->Rp, rs);
+      CPD_LAUNCH(h, "spmm row zeros");
+      if (h->Rp == 128)
+        rowsort_flat_kernel<128><<<h->num_sms * 2, 512, 0, st>>>(a, Y, rs);
+      else
+        rowsort_flat_kernel<0><<<h->num_sms * 2, 512, 0, st>>>(a, Y, rs);
+      CPD_LAUNCH(h, "spmm rows");
+      c_begin = (int64_t)h->rs_cap / 32;    // then the positions past the sorted lists
+    }
+    const int hb = sorted ? 1 : 0;
     switch (h->Rp) {
-      case 16: spmm_kernel<16><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
-      case 32: spmm_kernel<32><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
-      case 64: spmm_kernel<64><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
-      case 128: spmm_kernel<128><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
-      default: spmm_kernel<0><<<grid, block, shm, st>>>(a, Y, out_nnz_sel); break;
+      case 16: spmm_kernel<16><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
+      case 32: spmm_kernel<32><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
+      case 64: spmm_kernel<64><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
+      case 128: spmm_kernel<128><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
+      default: spmm_kernel<0><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
     }
     CPD_LAUNCH(h, "spmm");
   }

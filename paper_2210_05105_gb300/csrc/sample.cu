@@ -16,14 +16,14 @@ namespace {
 constexpr int LEV_THREADS = 256;
 
 // ell_i = u_i^T X u_i with X = G_k^+ (Algorithm 2 line 2) as
-// sum_{a<=b} c_ab X_ab u_a u_b (c = 1 on the diagonal, 2 off it).  One row
-// per thread; the block's 256 rows sit column-major in shared memory
-// (conflict-free), the coefficients split into float32 hi + lo (all threads
-// read the same entry: broadcast).  Each product u_a u_b is formed exactly
-// (TwoProduct) and the sum is carried in df64 on the float32 pipes, i.e. to
-// ~2^-48 relative instead of float64 FMAs at 1/64 rate.  Also writes the sum
-// of each block's scores.  (The tile's row stride 257 keeps the transposing
-// stores free of bank conflicts.)
+// sum_a u_a v_a, v_a = sum_{b>=a} c_ab X_ab u_b (c = 1 on the diagonal, 2 off
+// it).  One row per thread; the block's 256 rows sit column-major in shared
+// memory (conflict-free), the coefficients split into float32 hi + lo (all
+// threads read the same entry: broadcast).  Each v_a and the outer sum are
+// Dot2 compensated dot products (exact leading products, TwoSum) in df64 on
+// the float32 pipes, i.e. to ~2^-48 relative instead of float64 FMAs at 1/64
+// rate.  Also writes the sum of each block's scores.  (The tile's row stride
+// 257 keeps the transposing stores free of bank conflicts.)
 // SPLIT threads share a row: thread part h takes rows a = h, h + SPLIT, ...
 // of the triangle, and part 0 merges the partial double-floats in part order
 // (deterministic).  With ROWS = 2 a thread carries rows t and t + 128 of the
@@ -77,44 +77,40 @@ __global__ void __launch_bounds__(LEV_THREADS / ROWS * SPLIT) lev_kernel(const f
       }
     }
   } else {
-    // per row two independent df64 chains (even and odd b) for
-    // instruction-level parallelism, merged at the end
-    float lh2[ROWS], ll2[ROWS];
-#pragma unroll
-    for (int q = 0; q < ROWS; ++q) { lh2[q] = 0.0f; ll2[q] = 0.0f; }
+    // Horner-like split of the quadratic form: for each a the inner sum
+    // v_a = sum_{b >= a} X'_ab u_b is a compensated dot product (the Dot2
+    // step of Ogita, Rump and Oishi: exact leading product, TwoSum into
+    // vh, all rounding errors and the X'_ab low parts gathered in vl), then
+    // l += u_a v_a by the same step.  Per term 11 float32 operations instead
+    // of 14 for accumulating each exact product u_a u_b X'_ab into l.  Even
+    // and odd b run as two independent chains, merged per a.
     for (int a = h; a < R; a += SPLIT) {
       int p = a * R - a * (a - 1) / 2;
-      float ua[ROWS];
+      float vh[ROWS], vl[ROWS], vh2[ROWS], vl2[ROWS];
 #pragma unroll
-      for (int q = 0; q < ROWS; ++q) ua[q] = us[a * (LEV_THREADS + 1) + t + q * RT];
+      for (int q = 0; q < ROWS; ++q) { vh[q] = 0.0f; vl[q] = 0.0f; vh2[q] = 0.0f; vl2[q] = 0.0f; }
       int b = a;
       for (; b + 1 < R; b += 2, p += 2) {
         const float2 x0 = Xs[p], x1 = Xs[p + 1];
 #pragma unroll
         for (int q = 0; q < ROWS; ++q) {
           const float ub0 = us[b * (LEV_THREADS + 1) + t + q * RT], ub1 = us[(b + 1) * (LEV_THREADS + 1) + t + q * RT];
-          const float ph0 = __fmul_rn(ua[q], ub0), ph1 = __fmul_rn(ua[q], ub1);
-          const float pl0 = __fmaf_rn(ua[q], ub0, -ph0), pl1 = __fmaf_rn(ua[q], ub1, -ph1);
-          df_fma(lh[q], ll[q], ph0, x0.x);
-          df_fma(lh2[q], ll2[q], ph1, x1.x);
-          ll[q] = __fmaf_rn(pl0, x0.x, __fmaf_rn(ph0, x0.y, ll[q]));
-          ll2[q] = __fmaf_rn(pl1, x1.x, __fmaf_rn(ph1, x1.y, ll2[q]));
+          df_dot_step_f(vh[q], vl[q], x0.x, x0.y, ub0);
+          df_dot_step_f(vh2[q], vl2[q], x1.x, x1.y, ub1);
         }
       }
       if (b < R) {
         const float2 x = Xs[p];
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-          const float ub = us[b * (LEV_THREADS + 1) + t + q * RT];
-          const float ph = __fmul_rn(ua[q], ub);
-          const float pl = __fmaf_rn(ua[q], ub, -ph);
-          df_fma(lh[q], ll[q], ph, x.x);
-          ll[q] = __fmaf_rn(pl, x.x, __fmaf_rn(ph, x.y, ll[q]));
-        }
+        for (int q = 0; q < ROWS; ++q) df_dot_step_f(vh[q], vl[q], x.x, x.y, us[b * (LEV_THREADS + 1) + t + q * RT]);
+      }
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) {
+        df_merge(vh[q], vl[q], vh2[q], vl2[q]);
+        df_renorm(vh[q], vl[q]);
+        df_dot_step_f(lh[q], ll[q], vh[q], vl[q], us[a * (LEV_THREADS + 1) + t + q * RT]);
       }
     }
-#pragma unroll
-    for (int q = 0; q < ROWS; ++q) df_merge(lh[q], ll[q], lh2[q], ll2[q]);
   }
   if (SPLIT > 1) {
     if (h > 0)
@@ -282,7 +278,10 @@ size_t lev_smem(int R) {
   return (size_t)npairs * 8 + (size_t)(LEV_THREADS + 1) * cpd_pad4(R) * 4;
 }
 
-int lev_split(int R) { return R > 64 ? 8 : R > 32 ? 4 : 1; }
+#ifndef CPD_LEV_SPLIT_WIDE
+#define CPD_LEV_SPLIT_WIDE 8     // threads a row for R > 64 (4 or 8)
+#endif
+int lev_split(int R) { return R > 64 ? CPD_LEV_SPLIT_WIDE : R > 32 ? 4 : 1; }
 
 cpd_status quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
                         double* cdf) {

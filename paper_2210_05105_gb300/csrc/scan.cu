@@ -3,6 +3,7 @@
 // (sort nonzeros by KRP-row key, number the fibers) and the flat work list of
 // the sampled MTTKRP.
 #include "common.cuh"
+#include <algorithm>
 
 namespace {
 
@@ -182,6 +183,23 @@ cpd_status cpd_scan_u32(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n
   scan_down_kernel<<<(unsigned)nb, SCAN_THREADS, 0, h->stream>>>(in, out, n, bsum);
   CPD_LAUNCH(h, "scan kernels");
   CPD_CUDA(h, cudaFreeAsync(bsum, h->stream));
+  return CPD_OK;
+}
+
+// The same scan with caller scratch bsum of ceil(n / 2048) words (no
+// allocation, so it can be captured in a graph).
+int64_t cpd_scan_u32_scratch(int64_t n) { return cpd_ceil_div(std::max<int64_t>(n, 1), SCAN_TILE); }
+cpd_status cpd_scan_u32_buf(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
+                            uint32_t* bsum, cudaStream_t st) {
+  if (n <= 0) {
+    if (total) CPD_CUDA(h, cudaMemsetAsync(total, 0, sizeof(uint32_t), st));
+    return CPD_OK;
+  }
+  const int64_t nb = cpd_ceil_div(n, SCAN_TILE);
+  scan_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, bsum);
+  scan_single_kernel<<<1, 1024, 0, st>>>(bsum, nb, total);
+  scan_down_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, bsum);
+  CPD_LAUNCH(h, "scan kernels");
   return CPD_OK;
 }
 

@@ -146,6 +146,43 @@ def test_sampled_mttkrp_hot_rows(cpd, R, bps):
     h.close()
 
 
+@pytest.mark.parametrize("R,dims,bps", [(100, (300_000, 400, 300), 0), (128, (250_000, 40, 30), 8)])
+def test_row_sorted_sampled_mttkrp_matches_oracle(cpd, R, dims, bps):
+    """With R > 64, a mode whose output Y (I_0 x Rp floats, 120-128 MB)
+    exceeds 96 MB takes the row-sorted SpMM: selected nonzeros counting-sorted
+    by output row, each row summed in registers and stored once, or reduced
+    once per 32-position chunk into stored zeros where it crosses a chunk
+    boundary (the Zipf-hot rows).  The second case (1,200 KRP rows, so nearly
+    every nonzero is selected; rows of up to ~1,200 nonzeros; 8 blocks per SM)
+    runs the kernel compiled for Rp = 128.  Equal to the oracle within 1e-5
+    for that mode and the unsorted ones, with the sorted lists holding all
+    selected nonzeros and capped at 1024 (the rest through the flat-list
+    SpMM afterwards)."""
+    nnz, J = 400_000, 6000
+    idx, vals, init = make_case(dims, nnz, R, seed=79, zipf=1.05)
+    fs = None
+    for cap in (0, 1000):
+        h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),
+                           [torch.from_numpy(u).cuda() for u in init], method="arls", rank=R, samples=J, seed=8,
+                           nnz_sel_capacity=cap, spmm_blocks_per_sm=bps)
+        if fs is None:
+            fs = gpu_factors(cpd, h)
+        for mode in range(3):
+            oi, op = _oracle_samples(fs, mode, J, 17, 0)
+            w = 1.0 / (J * op)
+            Y, nsel = cpd.cpd_sampled_mttkrp(h, mode, torch.from_numpy(oi), torch.from_numpy(w))
+            ref = oc.sampled_mttkrp(idx, vals, dims, fs, mode, oi, w)
+            assert rel_frob(Y.cpu().numpy(), ref) <= 1e-5, (cap, mode)
+            assert nsel == oc.selected_nnz(idx, dims, mode, oi)
+            if mode == 0:
+                assert nsel > 1024
+                # rows both inside one 32-position chunk and across chunks
+                skeys = np.unique(oc.krp_key(oi, dims, 0))
+                per_row = np.bincount(idx[0][np.isin(oc.krp_key(idx, dims, 0), skeys)], minlength=dims[0])
+                assert np.count_nonzero(per_row > 32) > 10 and np.count_nonzero(per_row == 1) > 1000
+        h.close()
+
+
 def test_sampled_mttkrp_edge_cases(cpd):
     h, idx, vals, init, cfg = _small(cpd)
     fs = gpu_factors(cpd, h)
