@@ -128,6 +128,8 @@ struct cpd_ctx {
 
   std::vector<void*> allocs;
 
+  float2* lev_xs = nullptr;            // R(R+1)/2: the leverage kernel's coefficients (float32 hi + lo)
+
   // row-sorted sampled SpMM (R > 64, modes whose output Y exceeds 96 MB)
   int64_t rs_cap = 0;                  // selected nonzeros the sorted lists hold (multiple of 32)
   uint32_t* rs_cnt = nullptr;          // Imax + 1: per-row counts, counted down again by the scatter

@@ -200,9 +200,15 @@ __global__ void __launch_bounds__(DTHREADS) normalize_gram_kernel(
 #ifndef CPD_GB_MINB
 #define CPD_GB_MINB 2            // resident blocks per SM the register budget is sized for
 #endif
-constexpr int GB_TR = 128;
+#ifndef CPD_GB_TR
+#define CPD_GB_TR 128
+#endif
+#ifndef CPD_GB_MAXT
+#define CPD_GB_MAXT 416
+#endif
+constexpr int GB_TR = CPD_GB_TR;
 constexpr int GB_FLUSH = 1024 / GB_TR;
-constexpr int GB_MAXT = 416;   // threads: one row group of nblk <= 406 blocks (R <= 112), 16 chains each
+constexpr int GB_MAXT = CPD_GB_MAXT;   // threads: one row group of nblk <= 406 blocks (R <= 112), 16 chains each
 __global__ void __launch_bounds__(GB_MAXT, CPD_GB_MINB) gram_blk_kernel(
     const float* __restrict__ Uin, float* __restrict__ Uout, int64_t I, int R, int Rp,
     const double* __restrict__ sigma, int do_scale, double* __restrict__ gpart, int nrg) {
@@ -211,15 +217,15 @@ __global__ void __launch_bounds__(GB_MAXT, CPD_GB_MINB) gram_blk_kernel(
   // [j * blockDim + t] for entry j: conflict-free), the tile after them
   double* acc64 = reinterpret_cast<double*>(gbs4);
   float* tile = reinterpret_cast<float*>(acc64 + 16 * blockDim.x);   // TR x Rp, row-major
-  __shared__ float inv[CPD_MAX_RANK];
+  __shared__ __align__(16) float inv[CPD_MAX_RANK];                 // read as float4
   __shared__ unsigned char ba[CPD_MAX_RANK / 4 * (CPD_MAX_RANK / 4 + 1) / 2];
   __shared__ unsigned char bb[CPD_MAX_RANK / 4 * (CPD_MAX_RANK / 4 + 1) / 2];
   const int t = threadIdx.x;
   const int nb4 = Rp / 4;
   const int nblk = nb4 * (nb4 + 1) / 2;
-  for (int r = t; r < R; r += blockDim.x) {
-    double sv = do_scale ? sigma[r] : 0.0;
-    inv[r] = (sv > 0.0) ? (float)(1.0 / sv) : 1.0f;
+  for (int r = t; r < Rp; r += blockDim.x) {     // 0 for the padding columns
+    double sv = do_scale && r < R ? sigma[r] : 0.0;
+    inv[r] = r >= R ? 0.0f : (sv > 0.0) ? (float)(1.0 / sv) : 1.0f;
   }
   for (int e = t; e < nblk; e += blockDim.x) {
     int a = 0, rem = e;
@@ -228,6 +234,11 @@ __global__ void __launch_bounds__(GB_MAXT, CPD_GB_MINB) gram_blk_kernel(
     bb[e] = (unsigned char)(a + rem);
   }
   __syncthreads();
+  // tile loads as 16-byte vectors: thread t takes vector t % nb4 of rows
+  // t / nb4, + lstep, ... (threads past lstep * nb4 load nothing)
+  const int lc4 = t % nb4, lstep = (int)blockDim.x / nb4;
+  const int lr0 = t / nb4 < lstep ? t / nb4 : GB_TR;
+  const float4 lsc = *reinterpret_cast<const float4*>(inv + 4 * lc4);
   const int bi = t % nblk, rg = t / nblk;
   const bool active = rg < nrg;
   const int a0 = 4 * ba[bi], b0 = 4 * bb[bi];
@@ -241,15 +252,15 @@ __global__ void __launch_bounds__(GB_MAXT, CPD_GB_MINB) gram_blk_kernel(
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t r0 = tl * GB_TR;
     __syncthreads();                             // previous tile consumed
-    for (int e = t; e < GB_TR * Rp; e += blockDim.x) {
-      const int rr = e / Rp, c = e % Rp;
+    for (int rr = lr0; rr < GB_TR; rr += lstep) {
       const int64_t i = r0 + rr;
-      float v = 0.0f;
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       if (i < I) {
-        if (c < R) v = Uin[i * Rp + c] * inv[c];
-        Uout[i * Rp + c] = v;
+        const float4 u = reinterpret_cast<const float4*>(Uin + i * Rp)[lc4];
+        v = make_float4(u.x * lsc.x, u.y * lsc.y, u.z * lsc.z, u.w * lsc.w);
+        reinterpret_cast<float4*>(Uout + i * Rp)[lc4] = v;
       }
-      tile[e] = v;
+      reinterpret_cast<float4*>(tile + rr * Rp)[lc4] = v;
     }
     __syncthreads();
     if (active) {
@@ -338,6 +349,7 @@ __device__ double block_sum_d(double v, double* red) {
 }
 
 constexpr int PINV_FAST_R = 64;
+constexpr int PINV_FAST_R2 = 104; // the fast path up to here: 12 entries a thread of 1024, 5 R^2 floats of shared memory
 constexpr int PINV_THREADS = 1024;
 constexpr int PINV_PER_T = 4;   // entries per thread of the fast path (R * R / 4 threads, at least one warp)
 
@@ -372,7 +384,7 @@ __device__ __forceinline__ dd dd_recip(dd a) {
   return dd_norm(s, __fadd_rn(e, c.l));
 }
 
-// Fast path for R <= 64 on the float32 pipes: Gauss-Jordan elimination in
+// Fast path for R <= 104 on the float32 pipes: Gauss-Jordan elimination in
 // df64 (G split exactly into float32 hi + lo; each thread keeps its own
 // entries in registers, the owners of row and column k publish them, one
 // barrier per step) gives X ~ G^{-1} to ~cond(G) 2^-44; Newton-Schulz steps
@@ -384,10 +396,11 @@ __device__ __forceinline__ dd dd_recip(dd a) {
 // (nothing written) when a pivot is at most 1e-9 * max diag (the same test
 // as the float64 elimination, so the eigen-decomposition decides) or max |W|
 // does not reach 1e-7 within the allowed steps.
+template <int PT>   // entries per thread: R * R <= PT * blockDim
 __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
-  __shared__ float2 rowk[2][PINV_FAST_R], colk[2][PINV_FAST_R];
+  __shared__ float2 rowk[2][PINV_FAST_R2], colk[2][PINV_FAST_R2];
   __shared__ float red[32];
-  const int t = threadIdx.x, nt = blockDim.x;   // R * R <= PINV_PER_T * nt
+  const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
   float* Gh = sm;
   float* Gl = Gh + RR;
@@ -402,37 +415,38 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     Gh[e] = hi;
     Gl[e] = (float)(v - (double)hi);
   }
-  int ei[PINV_PER_T], ej[PINV_PER_T];
-  dd w[PINV_PER_T];
+  int eij[PT];   // (row << 16) | column of each entry, -1 past R * R
+  dd w[PT];
 #pragma unroll
-  for (int m = 0; m < PINV_PER_T; ++m) {
+  for (int m = 0; m < PT; ++m) {
     const int e = t + m * nt;
-    ei[m] = e < RR ? e / R : -1;
-    ej[m] = e < RR ? e - ei[m] * R : -1;
+    eij[m] = e < RR ? ((e / R) << 16) | (e % R) : -1;
   }
   __syncthreads();
 #pragma unroll
-  for (int m = 0; m < PINV_PER_T; ++m) {
+  for (int m = 0; m < PT; ++m) {
     const int e = t + m * nt;
-    w[m] = ei[m] >= 0 ? dd{Gh[e], Gl[e]} : dd{0.0f, 0.0f};
+    w[m] = eij[m] >= 0 ? dd{Gh[e], Gl[e]} : dd{0.0f, 0.0f};
   }
   float maxd = 0.0f;
   for (int a = 0; a < R; ++a) maxd = fmaxf(maxd, fabsf(Gh[a * R + a]));
   for (int k = 0; k < R; ++k) {
     const int b = k & 1;
 #pragma unroll
-    for (int m = 0; m < PINV_PER_T; ++m) {
-      if (ei[m] == k) rowk[b][ej[m]] = make_float2(w[m].h, w[m].l);
-      if (ej[m] == k) colk[b][ei[m]] = make_float2(w[m].h, w[m].l);
+    for (int m = 0; m < PT; ++m) {
+      if (eij[m] < 0) continue;
+      const int i = eij[m] >> 16, j = eij[m] & 0xffff;
+      if (i == k) rowk[b][j] = make_float2(w[m].h, w[m].l);
+      if (j == k) colk[b][i] = make_float2(w[m].h, w[m].l);
     }
     __syncthreads();
     const dd piv{rowk[b][k].x, rowk[b][k].y};
     if (!(piv.h > 1e-9f * maxd) || !isfinite(piv.h)) return false;    // uniform
     const dd inv = dd_recip(piv);
 #pragma unroll
-    for (int m = 0; m < PINV_PER_T; ++m) {
-      const int i = ei[m], j = ej[m];
-      if (i < 0) continue;
+    for (int m = 0; m < PT; ++m) {
+      if (eij[m] < 0) continue;
+      const int i = eij[m] >> 16, j = eij[m] & 0xffff;
       const dd rj{rowk[b][j].x, rowk[b][j].y}, ci{colk[b][i].x, colk[b][i].y};
       // branch-free step: the pivot column is treated as the identity column
       // (r_k := 1, w := 0 there), so every entry runs the same instructions
@@ -445,8 +459,8 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     }
   }
 #pragma unroll
-  for (int m = 0; m < PINV_PER_T; ++m)
-    if (ei[m] >= 0) { Xh[t + m * nt] = w[m].h; Xl[t + m * nt] = w[m].l; }
+  for (int m = 0; m < PT; ++m)
+    if (eij[m] >= 0) { Xh[t + m * nt] = w[m].h; Xl[t + m * nt] = w[m].l; }
   __syncthreads();
   bool ok = false;
   for (int it = 0; it < max_newton && !ok; ++it) {
@@ -475,9 +489,9 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     for (int q = 0; q < nt / 32; ++q) em = fmaxf(em, red[q]);
     if (!isfinite(em)) return false;
     // X <- X + X W (the correction is small: float32 suffices)
-    float corr[PINV_PER_T];
+    float corr[PT];
 #pragma unroll
-    for (int m = 0; m < PINV_PER_T; ++m) {
+    for (int m = 0; m < PT; ++m) {
       const int e = t + m * nt;
       float c = 0.0f;
       if (e < RR) {
@@ -488,7 +502,7 @@ __device__ bool pinv_fast(const PinvJob& jb, int R, float* sm, int max_newton) {
     }
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < PINV_PER_T; ++m) {
+    for (int m = 0; m < PT; ++m) {
       const int e = t + m * nt;
       if (e < RR) {
         float sh, se;
@@ -530,7 +544,10 @@ __device__ __forceinline__ bool pinv_body(const PinvJob& jb, int R, int fast) {
   __shared__ double rowk[CPD_MAX_RANK], colk[CPD_MAX_RANK];
   const int t = threadIdx.x, nt = blockDim.x;
   const int RR = R * R;
-  if (R <= PINV_FAST_R && pinv_fast(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6)) return true;
+  if (R <= PINV_FAST_R && pinv_fast<PINV_PER_T>(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6)) return true;
+  if (R > PINV_FAST_R && R <= PINV_FAST_R2 && (int)blockDim.x * 12 >= R * R &&
+      pinv_fast<12>(jb, R, reinterpret_cast<float*>(A), fast ? 1 : 6))
+    return true;
   for (int e = t; e < RR; e += nt) {
     double v = 1.0;
     for (int k = 0; k < jb.nin; ++k) v *= jb.in[k][e];
@@ -1090,7 +1107,7 @@ cpd_status cpd_renormalize_inputs(cpd_ctx* h) {
 
 static size_t pinv_smem(int R) {
   size_t slow = (size_t)R * R * sizeof(double);
-  size_t fast = R <= PINV_FAST_R ? (size_t)5 * R * R * sizeof(float) : 0;
+  size_t fast = R <= PINV_FAST_R2 ? (size_t)5 * R * R * sizeof(float) : 0;
   return std::max(slow, fast);
 }
 

@@ -38,9 +38,23 @@ constexpr int LEV_UNROLL = CPD_LEV_UNROLL;
 // (blockDim = SPLIT * LEV_THREADS / ROWS).  Large R gives each row R(R+1)/2
 // terms while the transposed tile limits a block per SM, so the split
 // supplies the warps that hide the df64 chains' latency.
+// The coefficients of the quadratic form once per launch: pair p of the
+// row-major upper triangle (a <= b) holds c_ab X_ab as float32 hi + lo.
+__global__ void lev_coef_kernel(const double* __restrict__ X, int R, float2* __restrict__ xs) {
+  const int npairs = R * (R + 1) / 2;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+    int a = 0, rem = p;
+    while (rem >= R - a) { rem -= R - a; ++a; }
+    const int b = a + rem;
+    const double x = (a == b ? 1.0 : 2.0) * X[a * R + b];
+    const float hi = (float)x;
+    xs[p] = make_float2(hi, (float)(x - (double)hi));
+  }
+}
+
 template <int SPLIT, int ROWS>
 __global__ void __launch_bounds__(LEV_THREADS / ROWS * SPLIT) lev_kernel(const float* __restrict__ U, int64_t I,
-                                                                         int R, int Rp, const double* __restrict__ X,
+                                                                         int R, int Rp, const float2* __restrict__ xg,
                                                                          double* __restrict__ ell,
                                                                          double* __restrict__ blk, int fast) {
   constexpr int RT = LEV_THREADS / ROWS;           // row slots per part
@@ -53,18 +67,15 @@ __global__ void __launch_bounds__(LEV_THREADS / ROWS * SPLIT) lev_kernel(const f
   __shared__ float2 partial[SPLIT > 1 ? SPLIT - 1 : 1][LEV_THREADS];
   const int tid = threadIdx.x;
   const int t = tid % RT, h = tid / RT;
-  for (int p = tid; p < npairs; p += NT) {
-    int a = 0, rem = p;
-    while (rem >= R - a) { rem -= R - a; ++a; }
-    const int b = a + rem;
-    const double x = (a == b ? 1.0 : 2.0) * X[a * R + b];
-    const float hi = (float)x;
-    Xs[p] = make_float2(hi, (float)(x - (double)hi));
-  }
+  for (int p = tid; p < npairs; p += NT) Xs[p] = xg[p];
   const int64_t r0 = (int64_t)blockIdx.x * LEV_THREADS;
-  for (int e = tid; e < LEV_THREADS * Rp; e += NT) {   // coalesced rows -> transposed tile
-    const int rr = e / Rp, c = e % Rp;
-    us[c * (LEV_THREADS + 1) + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
+  {
+    // coalesced rows -> transposed tile: thread tid takes column tid % 128
+    // (Rp <= 128) of rows tid / 128, + NT / 128, ...
+    const int c = tid & 127;
+    if (c < Rp)
+      for (int rr = tid >> 7; rr < LEV_THREADS; rr += NT >> 7)
+        us[c * (LEV_THREADS + 1) + rr] = (r0 + rr < I) ? U[(r0 + rr) * Rp + c] : 0.0f;
   }
   __syncthreads();
   // rows t + q RT of the block, q < ROWS
@@ -312,16 +323,19 @@ int lev_split(int R) { return R > 64 ? CPD_LEV_SPLIT_WIDE : R > 32 ? 4 : 1; }
 
 cpd_status quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double* X, double* q, double* blk,
                         double* cdf) {
+  lev_coef_kernel<<<(h->R * (h->R + 1) / 2 + 255) / 256, 256, 0, h->stream>>>(X, h->R, h->lev_xs);
+  CPD_LAUNCH(h, "lev coefficients");
+  const float2* xg = h->lev_xs;
   const int64_t nb = cpd_ceil_div(I, LEV_THREADS);
   const int sp = lev_split(h->R);
   if (sp == 8)          // R > 64: two rows a thread, 8 parts
-    lev_kernel<8, 2><<<(unsigned)nb, LEV_THREADS / 2 * 8, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+    lev_kernel<8, 2><<<(unsigned)nb, LEV_THREADS / 2 * 8, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, xg, q, blk,
                                                                                       h->opt.precision);
   else if (sp == 4)     // 32 < R <= 64
-    lev_kernel<4, 2><<<(unsigned)nb, LEV_THREADS / 2 * 4, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+    lev_kernel<4, 2><<<(unsigned)nb, LEV_THREADS / 2 * 4, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, xg, q, blk,
                                                                                       h->opt.precision);
   else
-    lev_kernel<1, 1><<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, X, q, blk,
+    lev_kernel<1, 1><<<(unsigned)nb, LEV_THREADS, lev_smem(h->R), h->stream>>>(U, I, h->R, h->Rp, xg, q, blk,
                                                                               h->opt.precision);
   CPD_LAUNCH(h, "lev");
   blk_scan_kernel<<<1, 1024, 0, h->stream>>>(blk, nb);
@@ -349,6 +363,10 @@ cpd_status cpd_quadform_cdf(cpd_ctx* h, const float* U, int64_t I, const double*
 // Kernels with more than 48 KB of dynamic shared memory need an opt-in (set
 // once, outside any stream capture).
 cpd_status cpd_sample_init(cpd_ctx* h) {
+  {
+    const cpd_status sa = cpd_alloc(h, &h->lev_xs, (size_t)h->R * (h->R + 1) / 2);
+    if (sa != CPD_OK) return sa;
+  }
   for (const void* f : {(const void*)lev_kernel<1, 1>, (const void*)lev_kernel<4, 2>, (const void*)lev_kernel<8, 2>}) {
     const cpd_status st_ = cpd_smem_attr(h, f, lev_smem(h->R));
     if (st_ != CPD_OK) return st_;
