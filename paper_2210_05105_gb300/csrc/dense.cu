@@ -860,10 +860,11 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
 }
 
 // ---- solve for 32 < R <= 128: register-tiled Y P ------------------------------
-// A block of 16 TY threads (TY x 16) computes tiles of 8 TY rows x NB columns
-// (NB = 64 or 128 >= Rp): thread (ty, tx) owns rows 8 ty .. 8 ty + 7 and
-// columns TC tx .. TC tx + TC - 1 (TC = NB / 16), 8 TC accumulators in
-// registers.  P = G^+ rounded to float32 (R x NB, zero past R) stays in shared
+// A block of TXN TY threads (TY x TXN) computes tiles of 8 TY rows x NB
+// columns (NB = 64, 112 or 128 >= Rp; TXN = 16, 14, 16): thread (ty, tx) owns
+// rows 8 ty .. 8 ty + 7 and columns TC tx .. TC tx + TC - 1 (TC = NB / TXN),
+// 8 TC accumulators in registers.  (NB = 112 saves the eighth of the FMAs that
+// NB = 128 spends on zero columns at R = 100.)  P = G^+ rounded to float32 (R x NB, zero past R) stays in shared
 // memory for the whole grid-stride loop; each tile of Y is staged transposed
 // (Rp x tile rows, consecutive lanes loading consecutive rows, so the
 // transposing stores do not conflict).  Per k the thread reads 8 values of Y
@@ -871,17 +872,18 @@ __global__ void __launch_bounds__(DTHREADS, 2) solve_lane_kernel(
 // o), a = 0..R-1.  The float32 accumulation bounds the error (about 2^-24
 // sum_a |y_a P_ac| per output); carrying G^+'s float32 remainder as a second
 // FMA per term did not reduce it measurably, so it is left out here.
-template <int NB, int TY>
-__global__ void __launch_bounds__(16 * TY, 2) solve_tile_kernel(
+template <int NB, int TY, int TXN>
+__global__ void __launch_bounds__(TXN * TY, 2) solve_tile_kernel(
     const float* __restrict__ Y, const float* __restrict__ P2, float* __restrict__ Uw, int64_t I, int R, int Rp,
     double* __restrict__ colpart) {
-  constexpr int TC = NB / 16;
-  constexpr int TM = 8 * TY, YS = TM + 4, NT = 16 * TY;
+  constexpr int TC = NB / TXN;
+  static_assert(TC % 4 == 0, "16-byte vectors of P");
+  constexpr int TM = 8 * TY, YS = TM + 4, NT = TXN * TY;
   extern __shared__ float4 sm4[];
   float* Ph = reinterpret_cast<float*>(sm4);     // R x NB
   float* Ys = Ph + R * NB;                       // Rp x YS (transposed tile; rows >= R hold Y's zero padding)
   __shared__ float wsq[TY][NB];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int t = threadIdx.x, tx = t % TXN, ty = t / TXN;
   for (int e = t; e < R * NB; e += NT) {
     const int a = e / NB, c = e % NB;
     Ph[e] = c < R ? P2[a * R + c] : 0.0f;
@@ -1168,21 +1170,28 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     else {
       // as many blocks as are resident together (two per SM up to R ~ 100,
       // where the tile and G^+ take 104 KB of shared memory a block)
-      const int nb = rb == 64 ? 64 : 128, ty = solve_tile_ty(R, nb);
+      const int nb = rb == 64 ? 64 : (R <= 112 ? 112 : 128), ty = solve_tile_ty(R, nb);
+      const int threads = nb == 112 ? 14 * ty : 16 * ty;
+      const void* fn = nb == 64 ? (const void*)solve_tile_kernel<64, 16, 16>
+                                : nb == 112 ? (const void*)solve_tile_kernel<112, 16, 14>
+                                            : (const void*)solve_tile_kernel<128, 16, 16>;
       const size_t sh = solve_tile_smem(R, nb, ty);
       int occ = 1;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &occ, nb == 64 ? (const void*)solve_tile_kernel<64, 16> : (const void*)solve_tile_kernel<128, 16>, 256,
-              sh) != cudaSuccess || occ < 1) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, sh) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 1;
       }
       nblk = (int)std::min<int64_t>(std::min<int64_t>((int64_t)occ * h->num_sms, h->gram_blocks),
                                     std::max<int64_t>(cpd_ceil_div(I, 8 * ty), 1));
       if (nb == 64)
-        solve_tile_kernel<64, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
+        solve_tile_kernel<64, 16, 16><<<nblk, threads, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp,
+                                                                        h->colsq);
+      else if (nb == 112)
+        solve_tile_kernel<112, 16, 14><<<nblk, threads, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp,
+                                                                         h->colsq);
       else
-        solve_tile_kernel<128, 16><<<nblk, 256, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
+        solve_tile_kernel<128, 16, 16><<<nblk, threads, sh, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp,
+                                                                         h->colsq);
     }
     CPD_LAUNCH(h, "solve");
     sigma_kernel<<<R, 256, 0, h->stream>>>(h->colsq, nblk, R, h->sigma);
@@ -1225,8 +1234,9 @@ cpd_status cpd_dense_init(cpd_ctx* h) {
       {(const void*)pinv_kernel, s2},              {(const void*)solve_kernel<16>, s3},
       {(const void*)solve_kernel<32>, s3},
       {(const void*)gram_blk_kernel, (size_t)16 * GB_MAXT * sizeof(double) + (size_t)GB_TR * CPD_MAX_RANK * sizeof(float)},
-      {(const void*)solve_tile_kernel<64, 16>, solve_tile_smem(std::min(R, 64), 64, 16)},
-      {(const void*)solve_tile_kernel<128, 16>, solve_tile_smem(R, 128, 16)}};
+      {(const void*)solve_tile_kernel<64, 16, 16>, solve_tile_smem(std::min(R, 64), 64, 16)},
+      {(const void*)solve_tile_kernel<112, 16, 14>, solve_tile_smem(std::min(R, 112), 112, 16)},
+      {(const void*)solve_tile_kernel<128, 16, 16>, solve_tile_smem(R, 128, 16)}};
   for (const auto& a : attrs) {
     const cpd_status st = cpd_smem_attr(h, a.first, a.second);
     if (st != CPD_OK) return st;
