@@ -235,17 +235,17 @@ __device__ __forceinline__ void spmm_warp(const MArgs& a, int Rp, int C, int E, 
                                           float scale, uint32_t useg, int cnt) {
   uint32_t cu = 0xffffffffu;
   float4 hv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  if (RPT && E * C == 32 && cnt == 32) {
-    // a full chunk and a lane-group shape that fills the warp: every step is
-    // valid (four steps unrolled at Rp >= 32, two at Rp = 16: more would
-    // spill at 32 registers)
+  if (RPT && (E * C == 32 || E == 1) && cnt == 32) {
+    // a full chunk and a lane-group shape that fills the warp (or one group
+    // of C < 32 lanes, the others idle): every step is valid (four steps
+    // unrolled at Rp >= 32, two at Rp = 16: more would spill at 32 registers)
 #pragma unroll (RPT >= 32 ? 4 : 2)
     for (int j0 = 0; j0 < 32; j0 += E) {
-      const int jj = j0 + sub;
+      const int jj = E == 1 ? j0 : j0 + sub;
       const uint32_t r = __shfl_sync(CPD_FULL, row, jj);
       const float sj = __shfl_sync(CPD_FULL, scale, jj);
       const uint32_t uj = __shfl_sync(CPD_FULL, useg, jj);
-      spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
+      if (E * C == 32 || sub < E) spmm_step(a, Rp, C, q, Hs, hot_acc, Y, r, sj, uj, cu, hv);
     }
   } else {
     for (int j0 = 0; j0 < cnt; j0 += E) {
@@ -599,7 +599,8 @@ static size_t spmm_smem(int threads, int n_hot, int Rp) {
 cpd_status cpd_spmm_init(cpd_ctx* h) {
   const size_t shm = spmm_smem(cpd_spmm_threads(1), cpd_spmm_hot_slots(h->Rp, 1), h->Rp);
   for (const void* f : {(const void*)spmm_kernel<0>, (const void*)spmm_kernel<16>, (const void*)spmm_kernel<32>,
-                        (const void*)spmm_kernel<64>, (const void*)spmm_kernel<128>}) {
+                        (const void*)spmm_kernel<64>, (const void*)spmm_kernel<100>,
+                        (const void*)spmm_kernel<128>}) {
     const cpd_status s = cpd_smem_attr(h, f, shm);
     if (s != CPD_OK) return s;
   }
@@ -719,6 +720,8 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
       CPD_LAUNCH(h, "spmm row zeros");
       if (h->Rp == 128)
         rowsort_flat_kernel<128><<<h->num_sms * 2, 512, 0, st>>>(a, Y, rs);
+      else if (h->Rp == 100)
+        rowsort_flat_kernel<100><<<h->num_sms * 2, 512, 0, st>>>(a, Y, rs);
       else
         rowsort_flat_kernel<0><<<h->num_sms * 2, 512, 0, st>>>(a, Y, rs);
       CPD_LAUNCH(h, "spmm rows");
@@ -729,6 +732,7 @@ cpd_status cpd_sampled_mttkrp_launch(cpd_ctx* h, int mode, const int32_t* idx, c
       case 16: spmm_kernel<16><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
       case 32: spmm_kernel<32><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
       case 64: spmm_kernel<64><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
+      case 100: spmm_kernel<100><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
       case 128: spmm_kernel<128><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
       default: spmm_kernel<0><<<grid, block, shm, st>>>(a, Y, out_nnz_sel, c_begin, hb); break;
     }
