@@ -410,8 +410,10 @@ def run_oracle(idx, vals, init, w, method, modes, threads=1):
 
 
 # ------------------------------------------------------------ byte models
-def algorithmic(phase, w, stats):
-    """Algorithmic bytes (or FP64 flops) per launch of a phase's kernel."""
+def algorithmic(phase, w, stats, fast=False):
+    """Algorithmic bytes (or float32 lane operations) per launch of a phase's
+    kernel.  fast: precision option 1, whose Gram and leverage terms are float32
+    (one FMA a Gram term; a multiply and an FMA a leverage term)."""
     N, R, J = len(w["dims"]), w["R"], w["J"]
     Rp = (R + 3) // 4 * 4
     if phase == "spmm":
@@ -423,7 +425,8 @@ def algorithmic(phase, w, stats):
     if phase in ("sampler", "gram"):
         # df64 terms of the quadratic forms (leverage scores) or Gram pairs,
         # R(R+1)/2 per row, as float32 lane operations
-        return "alu", stats["I_mean"] * R * (R + 1) / 2 * DF64_TERM_OPS
+        ops = (2 if phase == "sampler" else 1) if fast else DF64_TERM_OPS
+        return "alu", stats["I_mean"] * R * (R + 1) / 2 * ops
     if phase == "solve":
         # Y G+ with G+ rounded to float32: R^2 FMAs a row
         return "alu", stats["I_mean"] * R * R
@@ -435,9 +438,9 @@ def algorithmic(phase, w, stats):
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernel (`dram__bytes_read.sum + dram__bytes_write.sum`, two timed rounds of
+# kernel (`dram__bytes_read.sum + dram__bytes_write.sum`, mean over the mode updates of a timed round of
 # the same command line), keyed by (workload, method, phase).
-TRAFFIC_BYTES = {("zipf_1e5cube_50M", "arls", "spmm"): 67.94e6}
+TRAFFIC_BYTES = {("zipf_1e5cube_50M", "arls", "spmm"): 67.45e6}
 
 
 def profile_round(cpd, h, w, method, sweep_id):
@@ -592,7 +595,7 @@ def ours(args, world, rank, local):
     def roof(phase):
         ms, n_ = phases[phase]
         per_launch_ms = ms / max(n_, 1)
-        bound, amount = algorithmic(phase, w, stats)
+        bound, amount = algorithmic(phase, w, stats, fast=args.fast)
         if bound == "alu":
             ach = amount / (per_launch_ms / 1e3) / 1e12
             return {"phase": phase, "bound": "alu", "achieved": ach, "peak": FP32_LANE_TOPS,
