@@ -125,7 +125,8 @@ cpd_status cpd_default_options(cpd_options* opt);
  *                 uniforms from Philox4x64-10 with key (seed, 2) and counter
  *                 (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53,
  *                 u2 = top 53 bits of word 1 times 2^-53,
- *                 z = sqrt(-2 ln u1) cos(2 pi u2) in float64, rounded to float32.
+ *                 z = sqrt(-2 ln u1) cos(2 pi u2), evaluated in float32 (within
+ *                 a few float32 ulps of the value in float64 rounded to float32).
  *   cuda_stream   cudaStream_t the handle enqueues on (NULL: legacy stream).
  * The library copies and re-sorts the inputs (one layout per matricization,
  * sorted by KRP-row key, with a hash index from key to its nonzeros, Sec. 4.3)

@@ -61,10 +61,17 @@ __global__ void gauss_init_kernel(float* __restrict__ U, int64_t I, int R, int R
     const int r = (int)(e - i * R);
     unsigned long long c[4] = {(unsigned long long)i, (unsigned long long)r, (unsigned long long)k, 0ull};
     cpd_philox4x64(c, seed, CPD_STREAM_INIT);
-    const double u1 = (double)((c[0] >> 11) + 1ull) * 0x1.0p-53;
-    const double u2 = (double)(c[1] >> 11) * 0x1.0p-53;
-    const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
-    U[i * Rp + r] = (float)z;
+    // u1 = (top 53 bits of word 0 + 1) 2^-53 in (0, 1], u2 = top 53 bits of
+    // word 1 times 2^-53; z = sqrt(-2 ln u1) cos(2 pi u2) in float32 (the
+    // float64 transcendentals run at 1/64 of the float32 rate): ln u1 as
+    // log(u1) for u1 < 1/2 and log1p(-(1 - u1)) above, with 1 - u1 formed
+    // exactly, so both branches keep float32 relative accuracy; cos(2 pi u2)
+    // as cospi(2 u2).  Within a few float32 ulps of the binary64 definition.
+    const unsigned long long a1 = (c[0] >> 11) + 1ull;                 // u1 2^53, in [1, 2^53]
+    const float l = a1 < (1ull << 52) ? logf((float)((double)a1 * 0x1.0p-53))
+                                      : log1pf(-(float)((double)((1ull << 53) - a1) * 0x1.0p-53));
+    const float z = sqrtf(-2.0f * l) * cospif((float)((double)(c[1] >> 11) * 0x1.0p-52));
+    U[i * Rp + r] = z;
   }
 }
 

@@ -397,6 +397,7 @@ cpd_status cpd_exact_mttkrp_launch(cpd_ctx* h, int mode, float* Y);
 // scan.cu
 cpd_status cpd_scan_u32(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);
 int64_t cpd_scan_u32_scratch(int64_t n);
+cpd_status cpd_radix_init(cpd_ctx* h);
 cpd_status cpd_scan_u32_buf(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
                             uint32_t* bsum, cudaStream_t st);
 cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t n, int bits,

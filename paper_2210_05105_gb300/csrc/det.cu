@@ -214,6 +214,7 @@ __global__ void combine_kernel(const unsigned long long* __restrict__ rkeys, con
 
 cpd_status cpd_det_alloc(cpd_ctx* h) {
   cpd_status s;
+  if ((s = cpd_radix_init(h)) != CPD_OK) return s;
   h->sel_cap = h->opt.nnz_sel_capacity > 0 ? std::min<int64_t>(h->opt.nnz_sel_capacity, std::max<int64_t>(h->nnz, 1))
                                           : std::max<int64_t>(h->nnz, 1);
   const int64_t kc = std::max<int64_t>(h->Jcap, h->sel_cap);

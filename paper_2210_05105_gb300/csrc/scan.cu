@@ -121,21 +121,42 @@ __global__ void radix_hist_kernel(const unsigned long long* __restrict__ keys, i
 }
 
 // Stable scatter: element order inside a tile is (round, thread); ranks among
-// equal digits come from warp match masks, then a prefix over warps.
-__global__ void radix_scatter_kernel(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                     unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout,
-                                     int64_t n, int shift, const uint32_t* __restrict__ offs, int64_t nblk,
-                                     const uint32_t* __restrict__ n_dev) {
-  __shared__ uint32_t base[256];
-  if (n_dev) n = min(n, (int64_t)*n_dev);
+// equal digits come from warp match masks, then a prefix over warps.  The
+// tile is first reordered by digit in shared memory (its digit counts are the
+// differences of consecutive global offsets), then written out in that order,
+// so that each digit's run of the tile goes to consecutive addresses instead
+// of one scattered 8-byte write per key.
+constexpr size_t RS_SMEM = (size_t)RS_TILE * (sizeof(unsigned long long) + sizeof(uint32_t));
+__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
+    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offs, int64_t nblk,
+    const uint32_t* __restrict__ n_dev) {
+  extern __shared__ unsigned long long sk[];                       // RS_TILE keys, by digit
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + RS_TILE);         // RS_TILE payloads
+  __shared__ uint32_t gbase[256], lbase[256], base[256];
   __shared__ uint32_t wc[RS_WARPS][256];
+  if (n_dev) n = min(n, (int64_t)*n_dev);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  base[t] = offs[(int64_t)t * nblk + blockIdx.x];
+  const int64_t tile = (int64_t)blockIdx.x * RS_TILE;
+  // this tile's count of digit t: offsets are scanned in (digit, block) order
+  const int64_t oi = (int64_t)t * nblk + blockIdx.x;
+  const uint32_t g0 = offs[oi];
+  const uint32_t g1 = oi + 1 < 256 * nblk ? offs[oi + 1] : (uint32_t)n;
+  gbase[t] = g0;
+  lbase[t] = g1 - g0;
 #pragma unroll
   for (int w = 0; w < RS_WARPS; ++w) wc[w][t] = 0;
   __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {          // inclusive scan of the counts
+    const uint32_t v = t >= o ? lbase[t - o] : 0u;
+    __syncthreads();
+    lbase[t] += v;
+    __syncthreads();
+  }
+  lbase[t] -= g1 - g0;                          // exclusive: the digit's first slot in the tile
+  base[t] = lbase[t];
+  __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
-  int64_t tile = (int64_t)blockIdx.x * RS_TILE;
   for (int r = 0; r < RS_ROUNDS; ++r) {
     int64_t e = tile + (int64_t)r * RS_THREADS + t;
     bool valid = e < n;
@@ -155,14 +176,22 @@ __global__ void radix_scatter_kernel(const unsigned long long* __restrict__ kin,
     }
     __syncthreads();
     if (valid) {
-      uint32_t pos = wc[warp][d] + rank;
-      kout[pos] = k;
-      vout[pos] = v;
+      const uint32_t pos = wc[warp][d] + rank;   // slot in the tile
+      sk[pos] = k;
+      sv[pos] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) wc[w][t] = 0;
     __syncthreads();
+  }
+  const int64_t tn = n - tile < RS_TILE ? n - tile : RS_TILE;
+  for (int i = t; i < (int)tn; i += RS_THREADS) {
+    const unsigned long long k = sk[i];
+    const uint32_t d = (uint32_t)((k >> shift) & 255u);
+    const uint32_t pos = gbase[d] + ((uint32_t)i - lbase[d]);
+    kout[pos] = k;
+    vout[pos] = sv[i];
   }
 }
 
@@ -204,10 +233,18 @@ cpd_status cpd_scan_u32_buf(cpd_ctx* h, const uint32_t* in, uint32_t* out, int64
 }
 
 // Stable LSD radix sort of (keys, vals) on the low `bits` bits of the keys.
+// The scatter's shared-memory limit (its 48 KB tile beside its static
+// arrays); called at set-up, outside any stream capture.
+cpd_status cpd_radix_init(cpd_ctx* h) { return cpd_smem_attr(h, (const void*)radix_scatter_kernel, 64 * 1024); }
+
 // The sorted result ends in keys/vals; keys_tmp/vals_tmp are scratch of n.
 cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* vals, int64_t n, int bits,
                               unsigned long long* keys_tmp, uint32_t* vals_tmp) {
   if (n <= 1 || bits <= 0) return CPD_OK;
+  {
+    const cpd_status si = cpd_radix_init(h);
+    if (si != CPD_OK) return si;
+  }
   int64_t nblk = cpd_ceil_div(n, RS_TILE);
   uint32_t* counts = nullptr;
   CPD_CUDA(h, cudaMallocAsync((void**)&counts, (size_t)nblk * 256 * sizeof(uint32_t), h->stream));
@@ -220,8 +257,8 @@ cpd_status cpd_radix_sort_u64(cpd_ctx* h, unsigned long long* keys, uint32_t* va
     CPD_LAUNCH(h, "radix_hist");
     cpd_status s = cpd_scan_u32(h, counts, counts, nblk * 256, nullptr);
     if (s != CPD_OK) return s;
-    radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, va, kb, vb, n, shift, counts, nblk,
-                                                                       nullptr);
+    radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, RS_SMEM, h->stream>>>(ka, va, kb, vb, n, shift, counts, nblk,
+                                                                             nullptr);
     CPD_LAUNCH(h, "radix_scatter");
     unsigned long long* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
@@ -252,8 +289,8 @@ cpd_status cpd_radix_sort_u64_dev(cpd_ctx* h, unsigned long long* keys, uint32_t
       CPD_LAUNCH(h, "radix_hist");
       cpd_status s = cpd_scan_u32(h, counts, counts, nblk * 256, nullptr);
       if (s != CPD_OK) return s;
-      radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, 0, h->stream>>>(ka, va, kb, vb, cap, shift, counts, nblk,
-                                                                         n_dev);
+      radix_scatter_kernel<<<(unsigned)nblk, RS_THREADS, RS_SMEM, h->stream>>>(ka, va, kb, vb, cap, shift, counts,
+                                                                               nblk, n_dev);
       CPD_LAUNCH(h, "radix_scatter");
       unsigned long long* tk = ka; ka = kb; kb = tk;
       uint32_t* tv = va; va = vb; vb = tv;

@@ -542,8 +542,8 @@ def test_library_drawn_initial_factors_match_oracle_generator(cpd):
     """init_factors = NULL: the library draws U_k ~ N(0, 1) from the seed
     (Box-Muller on Philox4x64-10, key (seed, 2)); after the normalisation of
     Algorithm 1 line 2 they equal the oracle's draws from the same
-    definition to float32 rounding, and the handle then runs as if the caller
-    had passed those factors."""
+    definition (float64 there, float32 on the GPU) within 1e-6, and the
+    handle then runs as if the caller had passed those factors."""
     from oracle import philox as ph
     dims, R, J, seed = (230, 170, 90), 8, 1500, 4242
     idx, vals, _ = make_case(dims, 15000, R, seed=55)
