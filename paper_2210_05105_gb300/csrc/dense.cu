@@ -1065,11 +1065,18 @@ __global__ void __launch_bounds__(256) fit_fiber_kernel(FitFiberArgs a, const do
       // h = sigma * (rows of the other factors); key = sum_k i_k stride_k
       // in mixed radix over the modes k != m in increasing order
       float4 hv = sg;
+      const int klast = a.m == a.N - 1 ? a.N - 2 : a.N - 1;     // its index is what remains of the key
 #pragma unroll
       for (int k = 0; k < CPD_MAX_MODES; ++k) {
         if (k >= a.N || k == a.m) continue;
-        const int64_t ik = (int64_t)(key % (unsigned long long)a.dims[k]);
-        key /= (unsigned long long)a.dims[k];
+        int64_t ik;
+        if (k == klast) {
+          ik = (int64_t)key;
+        } else {
+          const unsigned long long qk = key / (unsigned long long)a.dims[k];
+          ik = (int64_t)(key - qk * (unsigned long long)a.dims[k]);
+          key = qk;
+        }
         const float4 u = reinterpret_cast<const float4*>(a.U[k] + ik * a.Rp)[q];
         hv.x *= u.x; hv.y *= u.y; hv.z *= u.z; hv.w *= u.w;
       }
