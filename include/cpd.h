@@ -75,10 +75,10 @@ typedef struct {
   int64_t nnz_sel_capacity; /* deterministic mode: most selected nonzeros one
                               downsampled MTTKRP may gather (its sorted work list is
                               sized from it); 0 = nnz.  More latches CPD_ERR_CAPACITY.
-                              Otherwise: length of the row-bucketed work list used for
-                              modes whose I_n x R output exceeds 64 MB; 0 = min(nnz,
-                              2^27).  Selected nonzeros past it are processed
-                              unbucketed (same result, no error) */
+                              Otherwise, for R > 64: length of the row-sorted work
+                              list (32 bytes an entry) of modes whose I_n x R output
+                              exceeds 96 MB; 0 = min(nnz, 2^27).  Selected nonzeros
+                              past it take the unsorted path (same result, no error) */
   int64_t reserved_i64[3];
   int32_t sketched_gram;   /* 0: solve with G = *_{k!=n} U_k^T U_k (Eq. 5, Sec. 4);
                               1: with the Gram of the sampled rows, sum_j w_j h_j h_j^T,
