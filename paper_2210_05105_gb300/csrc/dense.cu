@@ -958,8 +958,8 @@ static size_t solve_tile_smem(int R, int NB, int TY) {
   return ((size_t)R * NB + (size_t)cpd_pad4(R) * (8 * TY + 4)) * sizeof(float);
 }
 // 256-row tiles of 512 threads were measured slower than 128-row tiles of
-// 256 threads at R = 100 (22.6 against 20.0 ms a round at the billion-scale
-// workload), so TY = 16 is used throughout
+// 256 threads at R = 100 (22.6 against 20.0 ms a round for the factors of an
+// 8.2e6 x 1.77e5 x 8.1e6 tensor), so TY = 16 is used throughout
 static int solve_tile_ty(int R, int NB) { (void)R; (void)NB; return 16; }
 
 static int solve_rb(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
