@@ -64,7 +64,9 @@ def parse():
     p.add_argument("--workload", default="zipf_reddit_1B",
                    choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
     p.add_argument("--branches", type=int, default=16, help="concurrent branches of the batched graph")
-    p.add_argument("--leaf-rows", type=int, default=0, help="STS-CP rows per tree leaf F (0: F = R)")
+    p.add_argument("--leaf-rows", type=int, default=0,
+                   help="STS-CP rows per tree leaf F (0: the library's default, the smallest of 8, 16, 32 below R "
+                        "whose trees fit in 8 GB, else R)")
     p.add_argument("--autotune", action="store_true", help="run cpd_autotune on the handle before timing")
     p.add_argument("--no-autotune", action="store_true", help="batched workloads: keep the default launch shapes")
     p.add_argument("--no-e2e", action="store_true")
@@ -687,7 +689,7 @@ def ours(args, world, rank, local):
                 "config": {"workload": args.workload, "dims": list(dims), "nnz": w["nnz"], "zipf_s": w["zipf"],
                            "values": w["values"], "R": R, "J": J, "method": args.method,
                            "sketched_gram": args.sketched, "precision": "fast" if args.fast else "exact-draws",
-                           "leaf_rows": args.leaf_rows or R, "autotuned": tuned,
+                           "leaf_rows": args.leaf_rows or "library default", "autotuned": tuned,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MB write, outside the events)",
                            "generate_seconds": gen_s, "generator_draws": draws_used,

@@ -70,7 +70,8 @@ typedef struct {
   int32_t rank;            /* R */
   int64_t samples;         /* J, draws per mode update (capacity for caller lists) */
   uint64_t seed;           /* Philox4x64-10 key word 0 for all draws */
-  int32_t leaf_rows;       /* STS-CP rows per tree leaf F; 0 means F = R */
+  int32_t leaf_rows;       /* STS-CP rows per tree leaf F; 0: the smallest of 8, 16,
+                              32 (below R) whose trees take at most 8 GB, else R */
   int32_t input_on_host;   /* 1: idx, vals, init_factors of cpd_create are host memory */
   int64_t nnz_sel_capacity; /* deterministic mode: most selected nonzeros one
                               downsampled MTTKRP may gather (its sorted work list is

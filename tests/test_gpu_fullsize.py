@@ -100,11 +100,13 @@ def test_fullsize_three_round_fit_matches_oracle(full):
 
 
 def test_fullsize_sts_draws_match_oracle(full):
-    """STS-CP at the full size (leaf rows F = R = 32, a 12-level tree per
-    factor), in the launch configuration of `bench.py --method sts`: all
-    65,536 draws of a mode update equal the FP64 oracle's walk on the same
-    factors except at decisions within 1e-12 m(root) of a threshold (ties,
-    counted and printed), with probabilities to 1e-9 relative."""
+    """STS-CP at the full size, in the launch configuration of
+    `bench.py --method sts` (the library's default leaf size, 8 rows here: a
+    14-level tree per factor; the oracle's trees use F = R = 32, and the law
+    does not depend on F): all 65,536 draws of a mode update equal the FP64
+    oracle's walk on the same factors except at decisions within 1e-12 m(root)
+    of a threshold (ties, counted and printed), with probabilities to 1e-9
+    relative."""
     cpd, h_arls, idx, vals = full
     dims, R, J = W["dims"], W["R"], W["J"]
     fs32 = [cpd.cpd_get_factors(h_arls, k) for k in range(3)]
