@@ -109,7 +109,7 @@ typedef struct {
   int32_t reserved_i32[3];
 } cpd_options;
 
-/* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, F = R, device input. */
+/* Fill *opt with defaults: ARLS, R = 8, J = 2000, seed 0, leaf_rows 0 (the library picks F), device input. */
 cpd_status cpd_default_options(cpd_options* opt);
 
 /*
