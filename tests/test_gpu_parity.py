@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: sample indices exact except draws the oracle marks as ties
-within 1e-12 of a bin boundary; draw probabilities 1e-12 relative (float64
+within 1e-12 of a bin boundary, at most 1 in 1000 of them (counts printed); draw probabilities 1e-12 relative (float64
 on both sides); sampled and exact MTTKRP 1e-5 relative Frobenius (float32
 accumulation); solve / renormalisation 1e-5; fit 1e-9 absolute for a given
 model and 1e-3 between full randomized runs.
@@ -61,6 +61,19 @@ def test_arls_sampler_state_matches_oracle(cpd, R, dims):
     h.close()
 
 
+def _tie_mismatches(gi, oi, near, label):
+    """Draws whose indices differ from the oracle's: each must sit at a
+    near-tie (a target within the tolerance of a bin boundary, where the two
+    sides' rounding may legitimately pick either bin), and they must stay a
+    small minority (at most 1 in 1000, or 1).  The counts are printed."""
+    mism = np.any(gi != oi, axis=0)
+    J = gi.shape[1]
+    print("%s: %d draws, %d near ties, %d differing" % (label, J, int(near.sum()), int(mism.sum())))
+    assert not np.any(mism & ~near), "index mismatch away from a tie"
+    assert int(mism.sum()) <= max(1, J // 1000), "too many draws differ at ties"
+    return mism
+
+
 @pytest.mark.parametrize("mode,sweep", [(0, 0), (1, 3), (2, 7)])
 def test_arls_draws_match_oracle_exactly(cpd, mode, sweep):
     h, idx, vals, init, cfg = _small(cpd, J=20000)
@@ -69,8 +82,7 @@ def test_arls_draws_match_oracle_exactly(cpd, mode, sweep):
     gi, gp = cpd.cpd_leverage_sample(h, mode, cfg["J"], sweep)
     oi, op, near = oc.arls_draw(samplers, mode, cfg["J"], 3001, sweep)
     gi = gi.cpu().numpy()
-    mism = np.any(gi != oi, axis=0)
-    assert not np.any(mism & ~near), "index mismatch away from a tie"
+    mism = _tie_mismatches(gi, oi, near, "ARLS mode %d sweep %d" % (mode, sweep))
     assert np.all(gi[mode] == -1)
     ok = ~mism
     assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-12
@@ -92,8 +104,7 @@ def test_arls_draws_with_staged_running_sums(cpd, dims, mode):
     gi, gp = cpd.cpd_leverage_sample(h, mode, J, 5)
     oi, op, near = oc.arls_draw(samplers, mode, J, 77, 5)
     gi = gi.cpu().numpy()
-    mism = np.any(gi != oi, axis=0)
-    assert not np.any(mism & ~near), "index mismatch away from a tie"
+    mism = _tie_mismatches(gi, oi, near, "ARLS %s mode %d" % (dims, mode))
     ok = ~mism
     assert np.max(np.abs(gp.cpu().numpy()[ok] - op[ok]) / op[ok]) < 1e-12
     h.close()
@@ -253,7 +264,7 @@ def test_stepwise_sweep_matches_oracle(cpd):
             oi, op, near = oc.arls_draw(samplers, n, J, 3001, s)
             gi, gp = cpd.cpd_leverage_sample(h, n, J, s)
             gi = gi.cpu().numpy()
-            assert not np.any(np.any(gi != oi, axis=0) & ~near)
+            _tie_mismatches(gi, oi, near, "stepwise sweep %d mode %d" % (s, n))
             w = 1.0 / (J * gp.cpu().numpy())
             Y, _ = cpd.cpd_sampled_mttkrp(h, n, torch.from_numpy(gi), torch.from_numpy(w))
             Yo = oc.sampled_mttkrp(idx, vals, cfg["dims"], fs, n, gi, w)

@@ -38,6 +38,7 @@ def _compare(gi, gp, oi, op, near, label):
     print("%s: %d draws, %d near ties, %d differing (all at ties)" % (label, gi.shape[1], int(near.sum()),
                                                                        int(mism.sum())))
     assert not np.any(away), "STS draw differs away from a near-tie: %s" % np.nonzero(away)[0][:10]
+    assert int(mism.sum()) <= max(1, gi.shape[1] // 1000), "too many draws differ at ties"
     ok = ~mism
     return mism, np.max(np.abs(gp[ok] - op[ok]) / op[ok]) if ok.any() else 0.0
 
