@@ -254,9 +254,8 @@ cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out);
  * Downsampled MTTKRP without any device allocation (no counterpart in the
  * paper): the same result as cpd_sampled_mttkrp, for callers that cannot
  * allocate.  Meant for
- * code that must not call cudaMalloc: work enqueued while a stream is being
- * captured into a CUDA graph, code inside a framework whose memory pool
- * already owns the device memory, and latency-bound callers that cannot
+ * code that must not call cudaMalloc: code inside a framework whose memory
+ * pool already owns the device memory, and latency-bound callers that cannot
  * accept the implicit device synchronisation of cudaMalloc / cudaFree.  It
  * needs no cpd_handle (creating one allocates): the caller passes the COO
  * tensor and the factor matrices directly, and one pass over the nonzeros
@@ -274,11 +273,10 @@ cpd_status cpd_sweep_kernel_count(cpd_handle h, int64_t* out);
  * Scratch: a fixed 2 MiB table in the library's static device memory, held on
  * every GPU that loads the library until the process exits; J is limited to
  * 65,536 (CPD_ERR_CAPACITY beyond).  The first call on a device looks up the
- * table's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  All calls share the table and it keeps the
- * previous call's contents (each call clears it first), so calls whose GPU
- * work overlaps -- on different streams, or host threads -- race and must be
- * serialised by the caller.  Asynchronous on cuda_stream.
+ * table's device address (cudaGetSymbolAddress).  All calls share the table
+ * and it keeps the previous call's contents (each call clears it first), so
+ * calls whose GPU work overlaps -- on different streams, or host threads --
+ * race and must be serialised by the caller.  Asynchronous on cuda_stream.
  */
 cpd_status cpd_sampled_mttkrp_noalloc(int32_t N, const int64_t* dims, int64_t nnz,
                                       const int32_t* idx, const float* vals,

@@ -1,11 +1,10 @@
 // cpd_sampled_mttkrp_noalloc: the downsampled MTTKRP for callers that cannot
 // allocate device memory.
 //
-// Who needs it: code that runs while a CUDA stream is being captured into a
-// graph (a cudaMalloc there is refused or breaks the capture), code that
-// lives inside a framework whose caching allocator already owns the device
-// memory and hands out no more, and latency-bound callers for which the
-// implicit device synchronisation of cudaMalloc/cudaFree is unacceptable.
+// Who needs it: code that lives inside a framework whose caching allocator
+// already owns the device memory and hands out no more, and latency-bound
+// callers for which the implicit device synchronisation of cudaMalloc/cudaFree
+// is unacceptable.
 // They also may not hold a cpd_handle (creating one allocates), so this entry
 // point works directly on the caller's COO tensor and factor matrices.
 //

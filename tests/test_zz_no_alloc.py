@@ -1,6 +1,6 @@
 """cpd_sampled_mttkrp_noalloc, the allocation-free downsampled MTTKRP for
-callers that cannot call cudaMalloc (code running under stream capture, code
-whose device memory is owned by another allocator, latency-bound callers):
+callers that cannot call cudaMalloc (code whose device memory is owned by
+another allocator, latency-bound callers):
 called through the C ABI, its output must match the handle-based
 cpd_sampled_mttkrp and the FP64 oracle within the 1e-5 relative tolerance of
 the MTTKRP tests, on two calls in a row (the second call sees the first
