@@ -11,7 +11,7 @@
  *      tree of block Grams, Sec. 4.1 and Appendix B, Algorithms 4-5);
  *   2. computes the downsampled MTTKRP  Y = mat(T, n) S^T S U_{!=n}  (Eq. 7);
  *   3. solves  U_n = Y G^+  with G = *_{k != n} U_k^T U_k  (Eq. 4, Eq. 5) and
- *      renormalises the columns of U_n into sigma (Algorithm 1 lines 6-8).
+ *      renormalises the columns of U_n into sigma (Algorithm 1's mode update).
  *
  * Conventions shared by every entry point
  *   - Modes are 0-based; 1 <= N <= CPD_MAX_MODES.  Ranks 1 <= R <= CPD_MAX_RANK.
@@ -121,7 +121,7 @@ cpd_status cpd_default_options(cpd_options* opt);
  *   idx           N x nnz int32, mode-major (idx[k * nnz + e] = i_k of nonzero e).
  *   vals          nnz float32.
  *   init_factors  concatenated U_0 .. U_{N-1}, each I_k x R row-major float32
- *                 (the N(0,1) draws of Algorithm 1 line 1), or NULL: the library
+ *                 (the N(0,1) draws of Algorithm 1's initialisation), or NULL: the library
  *                 draws U_k[i, r] itself by the Box-Muller transform of two
  *                 uniforms from Philox4x64-10 with key (seed, 2) and counter
  *                 (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53,
@@ -131,7 +131,7 @@ cpd_status cpd_default_options(cpd_options* opt);
  *   cuda_stream   cudaStream_t the handle enqueues on (NULL: legacy stream).
  * The library copies and re-sorts the inputs (one layout per matricization,
  * sorted by KRP-row key, with a hash index from key to its nonzeros, Sec. 4.3)
- * and normalises the factors (Algorithm 1 lines 2-3).  Coordinates must be
+ * and normalises the factors (Algorithm 1's initialisation).  Coordinates must be
  * distinct (CPD_ERR_DUPLICATE otherwise).  Synchronises the stream.
  */
 cpd_status cpd_create(int32_t N, const int64_t* dims, int64_t nnz,
@@ -188,7 +188,7 @@ cpd_status cpd_exact_mttkrp(cpd_handle h, int32_t mode, float* Y);
 cpd_status cpd_gram_solve(cpd_handle h, int32_t mode, const float* Y, double* out_sigma);
 
 /*
- * n_sweeps ALS rounds (Algorithm 1 lines 4-9), each updating modes 0..N-1 in
+ * n_sweeps ALS rounds (Algorithm 1's outer loop), each updating modes 0..N-1 in
  * order with sample, MTTKRP and solve; sweep s of the handle (counted from 0
  * at creation) uses counter word s.  The first call captures one round as a
  * CUDA graph; later rounds replay it.

@@ -40,7 +40,7 @@ Readings of points the paper leaves open:
   real row is never entered.  At a leaf the target is rescaled by
   (sum of row masses) / m(leaf) and the smallest row with cumulative mass > t
   is taken (last row of nonzero mass if none).
-* Zero column norm at renormalisation (Algorithm 1 lines 6-7): sigma_r = 0 and
+* Zero column norm at renormalisation (Algorithm 1's mode update): sigma_r = 0 and
   the column is left unchanged.
 * Fit (Sec. 5.1): ||T - T~||^2 = ||T||^2 - 2 <T, T~> + sigma^T (*_k G_k) sigma,
   the last term exact for the dense model T~.
@@ -179,7 +179,7 @@ def selected_nnz(idx, dims, n, samp_idx):
 # ---------------------------------------------------------------------------
 
 def leverage_scores(U, Gk_pinv):
-    """dist_k = diag(U_k G_k^+ U_k^T) (Algorithm 2 line 2, Eq. 8 on one factor):
+    """dist_k = diag(U_k G_k^+ U_k^T) (Algorithm 2, Eq. 8 on one factor):
     row i is the dot product of row i of U_k G_k^+ with row i of U_k."""
     U = np.asarray(U, dtype=np.float64)
     return np.sum((U @ np.asarray(Gk_pinv, dtype=np.float64)) * U, axis=1)
@@ -407,7 +407,7 @@ def exact_krp_leverage(factors, n):
 
 
 # ---------------------------------------------------------------------------
-# Solve and renormalise (Eq. 4, Algorithm 1 lines 6-8)
+# Solve and renormalise (Eq. 4, Algorithm 1's mode update)
 # ---------------------------------------------------------------------------
 
 def solve_and_renorm(Y, G_pinv):
@@ -419,7 +419,7 @@ def solve_and_renorm(Y, G_pinv):
 
 
 def renormalize(U):
-    """Algorithm 1 line 2: divide each column by its 2-norm (zero columns kept)."""
+    """Algorithm 1's initial normalisation: divide each column by its 2-norm (zero columns kept)."""
     U = np.asarray(U, dtype=np.float64)
     nrm = np.sqrt(np.sum(U * U, axis=0))
     return U / np.where(nrm > 0, nrm, 1.0)[None, :]
@@ -476,7 +476,7 @@ def sample_weights(p, J):
 
 
 def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None, sketched=False):
-    """One subproblem of Algorithm 1 (lines 6-8) for mode n; updates state.
+    """One subproblem of Algorithm 1 (the update of mode n); updates state.
 
     state: dict with idx, vals, dims, factors (list of (I_k, R) float64),
     sigma, grams, and per method the sampler structures.
@@ -519,7 +519,7 @@ def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None, sketched=F
 
 
 def als_init(idx, vals, dims, init_factors, method, leaf_rows=None):
-    """Algorithm 1 lines 1-3 with caller-supplied N(0,1) draws."""
+    """Algorithm 1's initialisation with caller-supplied N(0,1) draws."""
     factors = [renormalize(U) for U in init_factors]
     R = factors[0].shape[1]
     state = {"idx": [np.asarray(a, dtype=np.int64) for a in idx],

@@ -96,7 +96,7 @@ STREAM_INIT = 2
 
 
 def gaussian_factors(dims, R, seed):
-    """Unit-variance Gaussian factors of Algorithm 1 line 1 drawn from the
+    """Unit-variance Gaussian factors of Algorithm 1's initialisation drawn from the
     same generator: entry (i, r) of U_k is the Box-Muller transform (Box and
     Muller, 1958) of two uniforms from Philox4x64-10 with key (seed, 2) and
     counter (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53 in (0, 1],

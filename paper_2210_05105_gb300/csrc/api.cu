@@ -49,7 +49,7 @@ __global__ void fill_kernel(double* p, int n, double v) {
 
 __global__ void bump_kernel(unsigned long long* ctr) { *ctr += 1ull; }
 
-// Algorithm 1 line 1 when the caller passes no initial factors: U_k[i, r]
+// Algorithm 1's initial factors when the caller passes none: U_k[i, r]
 // ~ N(0, 1) by the Box-Muller transform of two uniforms from Philox4x64-10,
 // key (seed, 2), counter (i, r, k, 0): u1 = (top 53 bits of word 0 + 1) 2^-53
 // in (0, 1], u2 = top 53 bits of word 1 times 2^-53,
@@ -75,7 +75,7 @@ __global__ void gauss_init_kernel(float* __restrict__ U, int64_t I, int R, int R
   }
 }
 
-// One mode update of Algorithm 1 (lines 6-8) on the handle's stream.
+// One mode update of Algorithm 1 on the handle's stream.
 // Pseudo-inverse of the Hadamard product of Grams for `mode` on the forked
 // side stream of a captured sweep (it depends only on the factor Grams, so it
 // overlaps the draws and the MTTKRP of the main branch).
@@ -98,7 +98,7 @@ cpd_status fork_pinv(cpd_ctx* h, int mode) {
   return CPD_OK;
 }
 
-// One mode update of Algorithm 1 (lines 6-8).  `forked`: G^+ of this mode was
+// One mode update of Algorithm 1.  `forked`: G^+ of this mode was
 // enqueued on the side stream and is joined before the solve.
 cpd_status mode_update(cpd_ctx* h, int n, bool forked = false) {
   cpd_status s;
@@ -259,7 +259,7 @@ cpd_status create_impl(cpd_ctx* h, int32_t N, const int64_t* dims, int64_t nnz, 
   if ((s = cpd_dense_init(h)) != CPD_OK) return s;
   if ((s = cpd_sample_init(h)) != CPD_OK) return s;
 
-  // Algorithm 1 lines 1-3: normalised factors, sigma = 1, sampler state
+  // Algorithm 1's initialisation: normalised factors, sigma = 1, sampler state
   if ((s = cpd_renormalize_inputs(h)) != CPD_OK) return s;
   fill_kernel<<<1, 128, 0, st>>>(h->sigma, R, 1.0);
   CPD_LAUNCH(h, "fill");

@@ -1,6 +1,6 @@
 // Dense kernels of the ALS update: Grams (Eq. 5 operands), Hadamard product
 // of Grams and its Moore-Penrose pseudo-inverse (Eq. 4-5), the solve
-// U_n = Y G^+ with column renormalisation (Algorithm 1 lines 6-8), and the
+// U_n = Y G^+ with column renormalisation (Algorithm 1's mode update), and the
 // fit of Sec. 5.1.
 //
 // Precision: factor storage and the solve GEMM are float32; Grams, the R x R
@@ -1179,7 +1179,7 @@ cpd_status cpd_gram(cpd_ctx* h, const float* U, int64_t I, double* G) {
   return gram_from(h, U, (float*)U, I, nullptr, 0, G);
 }
 
-// Algorithm 1 lines 2-3: normalise the columns of the initial factors.
+// Algorithm 1's initialisation: normalise the columns of the initial factors.
 cpd_status cpd_renormalize_inputs(cpd_ctx* h) {
   const int R = h->R;
   for (int k = 0; k < h->N; ++k) {

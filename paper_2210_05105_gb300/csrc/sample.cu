@@ -22,7 +22,7 @@ constexpr int LEV_THREADS = 256;
 // leverage scores and CDF of 8.2e6 rows at R = 100)
 constexpr int LEV_UNROLL = CPD_LEV_UNROLL;
 
-// ell_i = u_i^T X u_i with X = G_k^+ (Algorithm 2 line 2) as
+// ell_i = u_i^T X u_i with X = G_k^+ (Algorithm 2) as
 // sum_a u_a v_a, v_a = sum_{b>=a} c_ab X_ab u_b (c = 1 on the diagonal, 2 off
 // it).  One row per thread; the block's 256 rows sit column-major in shared
 // memory (conflict-free), the coefficients split into float32 hi + lo (all

@@ -101,7 +101,7 @@ def coo_values(nnz, seed, kind="uniform"):
 
 
 def init_factors(dims, R, seed):
-    """Unit-variance Gaussian initial factors (I_k, R) float32 (Algorithm 1 line 1)."""
+    """Unit-variance Gaussian initial factors (I_k, R) float32 (Algorithm 1's initialisation)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return [rng.standard_normal((int(I), R), dtype=np.float32) for I in dims]
 

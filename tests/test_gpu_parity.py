@@ -551,8 +551,8 @@ def test_duplicate_coordinates_summed_on_request(cpd):
 
 def test_library_drawn_initial_factors_match_oracle_generator(cpd):
     """init_factors = NULL: the library draws U_k ~ N(0, 1) from the seed
-    (Box-Muller on Philox4x64-10, key (seed, 2)); after the normalisation of
-    Algorithm 1 line 2 they equal the oracle's draws from the same
+    (Box-Muller on Philox4x64-10, key (seed, 2)); after Algorithm 1's initial
+    column normalisation they equal the oracle's draws from the same
     definition (float64 there, float32 on the GPU) within 1e-6, and the
     handle then runs as if the caller had passed those factors."""
     from oracle import philox as ph
@@ -589,7 +589,7 @@ def test_non_finite_gram_reports_singular_gram(cpd):
 
 @pytest.mark.parametrize("R", [40, 64, 99, 100, 128])
 def test_tiled_solve_large_rank_matches_oracle(cpd, R):
-    """Solve and renormalisation (Algorithm 1 lines 6-8) at 32 < R <= 128 (the
+    """Solve and renormalisation (Algorithm 1's mode update) at 32 < R <= 128 (the
     register-tiled kernel: 128-row tiles, ragged at 150 and 1031 rows, R not a
     multiple of 4 for R = 99) against the oracle's Y G^+ and column norms."""
     dims = (333, 150, 1031)

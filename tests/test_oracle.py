@@ -52,7 +52,7 @@ def test_uniform_mapping_range_and_resolution():
 
 
 def test_gaussian_factors_follow_the_normal_law():
-    """Library-side initial factors (Algorithm 1 line 1): the Box-Muller
+    """Library-side initial factors (Algorithm 1's initialisation): the Box-Muller
     transform of the Philox uniforms is N(0, 1) -- Kolmogorov-Smirnov against
     the normal CDF of scipy, first four moments, no infinities (u1 > 0) --
     and distinct factors, rows and columns get distinct counters."""
