@@ -56,11 +56,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--method", default="arls", choices=["arls", "sts", "exact"])
-    p.add_argument("--sketched", action="store_true", help="solve with the Gram of the draws (Fig. 2, bottom)")
+    p.add_argument("--sketched", action="store_true", help="solve with the Gram of the draws (Fig. 3, bottom)")
     p.add_argument("--fast", action="store_true", help="float32 Grams / leverage scores (precision option 1)")
     p.add_argument("--samples", type=int, default=0, help="override J of the workload")
     p.add_argument("--study-J", default="", help="comma-separated J values: print one line per J (runtime breakdown "
-                   "and fit after --steps sweeps), the sample-count study of the paper's Figs. 11-12")
+                   "and fit after --steps sweeps), the sample-count study of the paper's Figs. 12-13")
     p.add_argument("--workload", default="zipf_reddit_1B",
                    choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
     p.add_argument("--branches", type=int, default=16, help="concurrent branches of the batched graph")
@@ -493,7 +493,7 @@ def workload(args):
 
 
 def study_J(args):
-    """Runtime breakdown and fit against the sample count J (Figs. 11-12)."""
+    """Runtime breakdown and fit against the sample count J (Figs. 12-13)."""
     import torch
     from paper_2210_05105_gb300 import cpd
     w = workload(args)

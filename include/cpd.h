@@ -84,7 +84,7 @@ typedef struct {
   int32_t sketched_gram;   /* 0: solve with G = *_{k!=n} U_k^T U_k (Eq. 5, Sec. 4);
                               1: with the Gram of the sampled rows, sum_j w_j h_j h_j^T,
                               i.e. the normal equations of the downsampled problem
-                              (Fig. 2 bottom, G~^+) */
+                              (Fig. 3 bottom, G~^+) */
   int32_t precision;       /* 0: Grams, leverage scores and G^+ accurate to float64
                               (the inverse-CDF draws then equal a float64 statement
                               of Algorithm 3 up to ties); 1: fast: accumulated in
@@ -113,7 +113,7 @@ typedef struct {
 cpd_status cpd_default_options(cpd_options* opt);
 
 /*
- * Build a handle for the N-mode sparse tensor given as COO (Sec. 3: a list of
+ * Build a handle for the N-mode sparse tensor given as COO (Sec. 2: a list of
  * (N+1)-tuples).
  *   dims          host, N entries, 1 <= I_k < 2^31; for every n the product of the
  *                 other modes' I_k must be < 2^64 (column keys are 64-bit).
@@ -223,7 +223,7 @@ cpd_status cpd_get_arls_state(cpd_handle h, int32_t mode, double* ell, double* c
 cpd_status cpd_get_gram(cpd_handle h, int32_t mode, double* dst);
 
 /*
- * Phase timers (profiling aid; the paper's runtime breakdown of Sec. 5 into
+ * Phase timers (profiling aid; the paper's runtime breakdown of Sec. 5.4 into
  * sampling, MTTKRP and post-processing).  While enabled, step-wise entry
  * points bracket each kernel class with CUDA events on the handle's stream;
  * captured sweeps (cpd_als_sweep) are not timed.  cpd_profile_read

@@ -22,9 +22,9 @@ Conventions
 Readings of points the paper leaves open:
 * Moore-Penrose pseudo-inverse (Eq. 4): symmetric eigendecomposition,
   eigenvalues <= R * 2^-52 * lambda_max are treated as zero.
-* Sampling weight (Sec. 3.2, "extracts and reweights"): row j of S is
+* Sampling weight (Sec. 2.2 leaves the row scale of S unstated): row j of S is
   e_{row_j}^T / sqrt(J p_j), so S^T S carries weight w_j = 1 / (J p_j) on row_j;
-  draws are i.i.d. with replacement (Theorem 3.1).
+  draws are i.i.d. with replacement (Theorem 2.1).
 * Inverse-CDF draw (Algorithm 3, per factor): i = smallest index with
   CDF[i] > u * C; if rounding puts u * C at or past CDF[I-1], the first row
   whose running sum reaches C (the last row whose bin has nonzero width).
@@ -51,7 +51,7 @@ from .philox import draw_uniforms, STREAM_ARLS, STREAM_STS
 
 
 # ---------------------------------------------------------------------------
-# Khatri-Rao product rows and keys (Eq. 3, Fig. 2)
+# Khatri-Rao product rows and keys (Eq. 3, Fig. 3)
 # ---------------------------------------------------------------------------
 
 def krp_strides(dims, n):
@@ -135,7 +135,7 @@ def exact_mttkrp(idx, vals, dims, factors, n):
 
 
 def sampled_mttkrp(idx, vals, dims, factors, n, samp_idx, w):
-    """Downsampled MTTKRP mat(T, n) S^T S U_{!=n} (Eq. 7, Fig. 2 bottom).
+    """Downsampled MTTKRP mat(T, n) S^T S U_{!=n} (Eq. 7, Fig. 3 bottom).
 
     samp_idx: (N, J) sampled KRP rows (row n ignored); w: (J,) weights on the
     diagonal of S^T S.  S^T S is diagonal over KRP rows with entry
@@ -269,7 +269,7 @@ def arls_draw(samplers, n, J, seed, sweep, tie_tol=1e-12):
 
 def sts_build(U, F):
     """Binary tree over U_k: leaf v holds the Gram of its F-row block, each
-    internal node the sum of its children's matrices (Sec. 4.1, Fig. 4).
+    internal node the sum of its children's matrices (Sec. 4.1, Fig. 5).
 
     Heap layout: node 1 is the root, children of v are 2v and 2v+1, the L
     leaves (L a power of two >= ceil(I/F)) are nodes L..2L-1; leaf l covers
@@ -461,7 +461,7 @@ def fit(idx, vals, factors, sigma):
 
 def sketched_gram(factors, n, samp_idx, w):
     """Gram of the downsampled design matrix, (S U_{!=n})^T (S U_{!=n}) =
-    sum_j w_j h_j h_j^T over the draws (the G~ of Fig. 2, bottom)."""
+    sum_j w_j h_j h_j^T over the draws (the G~ of Fig. 3, bottom)."""
     h = krp_rows(factors, samp_idx, n)
     return h.T @ (np.asarray(w, dtype=np.float64)[:, None] * h)
 
@@ -482,7 +482,7 @@ def als_mode_update(state, n, method, J, seed, sweep, leaf_rows=None, sketched=F
     sigma, grams, and per method the sampler structures.
     Returns a dict of the intermediate quantities (samples, Y, G^+) so that
     tests can compare every step.  sketched=True solves with the Gram of the
-    drawn rows (the downsampled normal equations of Fig. 2, bottom) instead of
+    drawn rows (the downsampled normal equations of Fig. 3, bottom) instead of
     the Hadamard product of the factor Grams (Eq. 5).
     """
     idx, vals, dims, factors = state["idx"], state["vals"], state["dims"], state["factors"]

@@ -1,4 +1,4 @@
-// Downsampled MTTKRP  Y = mat(T, n) S^T S U_{!=n}  (Eq. 7, Fig. 2 bottom) and
+// Downsampled MTTKRP  Y = mat(T, n) S^T S U_{!=n}  (Eq. 7, Fig. 3 bottom) and
 // the exact MTTKRP of Eq. 6.
 //
 // Sampled path, two launches after clearing Y and the per-call tables:
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(512, 2) exact_kernel(MArgs a, const int32_t* _
 }
 
 // Rows of the downsampled design matrix S U_{!=n}: sqrt(w_j) h_j, one warp
-// per draw (their Gram is the sketched Gram of Fig. 2, bottom).
+// per draw (their Gram is the sketched Gram of Fig. 3, bottom).
 __global__ void sketch_rows_kernel(MArgs a, const int32_t* __restrict__ idx, const double* __restrict__ w, int64_t J,
                                    float* __restrict__ out) {
   const int lane = threadIdx.x & 31;

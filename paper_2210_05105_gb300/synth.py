@@ -4,7 +4,7 @@ This module only draws data: COO coordinates, values and the N(0,1) initial
 factors.  It holds none of the CP-ALS arithmetic, so the oracle and the CUDA
 library can both be fed from it without sharing any of the method's code.
 
-Recipe (stand-ins for the FROSTT tensors of the paper's Table 5, which are not
+Recipe (stand-ins for the FROSTT tensors of the paper's Table 4, which are not
 redistributed here):
 * Each mode index is pi_n(rank), rank drawn from a truncated Zipf law
   P(rank = r) proportional to (r + 1)^-s for r < I_n by inverse CDF over a
@@ -126,7 +126,7 @@ WORKLOADS = {
     "zipf_1e5cube_50M": dict(dims=(100_000, 100_000, 100_000), nnz=50_000_000, zipf=1.1,
                              values="lognormal", R=32, J=65536, sweeps=20,
                              data_seed=1002, init_seed=2002, sample_seed=3002),
-    # billion-scale 3-mode workload with Reddit's dims (paper Table 5): Zipf(1.3)
+    # billion-scale 3-mode workload with Reddit's dims (paper Table 4): Zipf(1.3)
     # per mode, log(1 + Poisson(3)) values; drawn on the device (libzipfgen)
     "zipf_reddit_1B": dict(dims=(8_200_000, 177_000, 8_100_000), nnz=1_000_000_000, zipf=1.3,
                            values="logpoisson", R=100, J=131072, sweeps=20, generator="device",

@@ -1,5 +1,5 @@
 """Parity of one mode update at the billion-scale workload (dims 8.2e6 x
-1.77e5 x 8.1e6 -- the Reddit tensor's dims, Table 5 -- 1e9 distinct Zipf(1.3)
+1.77e5 x 8.1e6 -- the Reddit tensor's dims, Table 4 -- 1e9 distinct Zipf(1.3)
 nonzeros, log(1 + Poisson(3)) values, R = 100, J = 2^17), in the launch
 configuration the bench times, after one captured ALS round:
 

@@ -388,7 +388,7 @@ def test_invalid_inputs_are_reported(cpd):
 
 def test_sketched_gram_solve_matches_oracle(cpd):
     """options.sketched_gram = 1: U_n = Y G~^+ with G~ the Gram of the draws
-    (Fig. 2, bottom), step by step against the oracle."""
+    (Fig. 3, bottom), step by step against the oracle."""
     dims, R, J = SMALL["dims"], SMALL["R"], SMALL["J"]
     idx, vals, init = make_case(dims, SMALL["nnz"], R, seed=1001)
     h = cpd.cpd_create(dims, torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(),

@@ -371,7 +371,7 @@ def test_randomized_als_noise_floor_scales_as_inverse_sqrt_J():
     """With the exact G^+ of Eq. 5 the sampled update is an unbiased estimate
     of the exact update (E[S^T S] = I), so on a planted exact-rank tensor the
     residual 1 - fit settles at a floor proportional to J^-1/2; STS-CP, which
-    draws from the exact leverage law (beta = 1 in Theorem 3.1), sits below
+    draws from the exact leverage law (beta = 1 in Theorem 2.1), sits below
     CP-ARLS-LEV at equal J."""
     dims = (9, 8, 7)
     idx, vals, _ = planted_dense(dims, 3, 31)
@@ -426,7 +426,7 @@ def test_sketched_gram_matches_explicit_sampling_matrix():
 
 
 def test_sketched_gram_als_solves_consistent_problems_exactly():
-    """With the downsampled normal equations (Fig. 2, bottom) an exactly
+    """With the downsampled normal equations (Fig. 3, bottom) an exactly
     rank-R tensor is a consistent least-squares problem: every full-rank
     sketch recovers the exact update, so the fit reaches 1 (no J^-1/2 floor,
     unlike the unbiased exact-G^+ update)."""
