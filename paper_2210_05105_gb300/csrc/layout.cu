@@ -219,6 +219,40 @@ int bits_for(unsigned long long maxval) {
   return b;
 }
 
+// The layout build's stream-ordered temporaries (32 bytes a nonzero): freed
+// in order on the success path (before its final synchronisation, so the pool
+// can return the memory), and by the destructor on every error return
+// (duplicate coordinates, an allocation that fails).
+struct StreamTemps {
+  cudaStream_t st;
+  void* p[7];
+  explicit StreamTemps(cudaStream_t s) : st(s) {
+    for (void*& q : p) q = nullptr;
+  }
+  template <typename T> cudaError_t alloc(T** q, size_t bytes, int slot) {
+    const cudaError_t e = cudaMallocAsync((void**)q, bytes, st);
+    if (e == cudaSuccess) p[slot] = (void*)*q;
+    return e;
+  }
+  cudaError_t release(int slot) {
+    void* q = p[slot];
+    p[slot] = nullptr;
+    return q ? cudaFreeAsync(q, st) : cudaSuccess;
+  }
+  cudaError_t release_all() {
+    cudaError_t first = cudaSuccess;
+    for (int k = 0; k < 7; ++k) {
+      const cudaError_t e = release(k);
+      if (first == cudaSuccess) first = e;
+    }
+    return first;
+  }
+  ~StreamTemps() {
+    for (void* q : p)
+      if (q && cudaFreeAsync(q, st) != cudaSuccess) (void)cudaGetLastError();
+  }
+};
+
 }  // namespace
 
 cpd_status cpd_build_layouts(cpd_ctx* h) {
@@ -227,8 +261,9 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
   cudaStream_t st = h->stream;
   const int grid = h->num_sms * 8, thr = 256;
 
+  StreamTemps tmp(st);
   int64_t* d_dims = nullptr;
-  CPD_CUDA(h, cudaMallocAsync((void**)&d_dims, sizeof(int64_t) * CPD_MAX_MODES, st));
+  CPD_CUDA(h, tmp.alloc(&d_dims, sizeof(int64_t) * CPD_MAX_MODES, 6));
   CPD_CUDA(h, cudaMemcpyAsync(d_dims, h->dims, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
   if (nnz > 0) {
     check_indices_kernel<<<grid, thr, 0, st>>>(h->idx, nnz, N, d_dims, h->vals, h->status);
@@ -237,7 +272,7 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
   int hs = 0;
   CPD_CUDA(h, cudaMemcpyAsync(&hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPD_CUDA(h, cudaStreamSynchronize(st));
-  CPD_CUDA(h, cudaFreeAsync(d_dims, st));
+  CPD_CUDA(h, tmp.release(6));
   if (hs != 0) {
     return cpd_fail(h, (cpd_status)hs, hs == CPD_ERR_OUT_OF_RANGE_INDEX ? "coordinate out of range"
                                                                       : "non-finite tensor value");
@@ -246,12 +281,12 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
   unsigned long long *keys = nullptr, *keys_tmp = nullptr;
   uint32_t *perm = nullptr, *perm_tmp = nullptr, *flags = nullptr, *fid = nullptr;
   size_t m = (size_t)std::max<int64_t>(nnz, 1);
-  CPD_CUDA(h, cudaMallocAsync((void**)&keys, m * 8, st));
-  CPD_CUDA(h, cudaMallocAsync((void**)&keys_tmp, m * 8, st));
-  CPD_CUDA(h, cudaMallocAsync((void**)&perm, m * 4, st));
-  CPD_CUDA(h, cudaMallocAsync((void**)&perm_tmp, m * 4, st));
-  CPD_CUDA(h, cudaMallocAsync((void**)&flags, m * 4, st));
-  CPD_CUDA(h, cudaMallocAsync((void**)&fid, m * 4, st));
+  CPD_CUDA(h, tmp.alloc(&keys, m * 8, 0));
+  CPD_CUDA(h, tmp.alloc(&keys_tmp, m * 8, 1));
+  CPD_CUDA(h, tmp.alloc(&perm, m * 4, 2));
+  CPD_CUDA(h, tmp.alloc(&perm_tmp, m * 4, 3));
+  CPD_CUDA(h, tmp.alloc(&flags, m * 4, 4));
+  CPD_CUDA(h, tmp.alloc(&fid, m * 4, 5));
 
   // duplicate_policy 1: order by coordinate once, sum repeated coordinates
   // into a compacted COO, then build every layout from it
@@ -394,12 +429,7 @@ cpd_status cpd_build_layouts(cpd_ctx* h) {
       }
     }
   }
-  CPD_CUDA(h, cudaFreeAsync(keys, st));
-  CPD_CUDA(h, cudaFreeAsync(keys_tmp, st));
-  CPD_CUDA(h, cudaFreeAsync(perm, st));
-  CPD_CUDA(h, cudaFreeAsync(perm_tmp, st));
-  CPD_CUDA(h, cudaFreeAsync(flags, st));
-  CPD_CUDA(h, cudaFreeAsync(fid, st));
+  CPD_CUDA(h, tmp.release_all());
   CPD_CUDA(h, cudaMemcpyAsync(&hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPD_CUDA(h, cudaStreamSynchronize(st));
   if (hs != 0) return cpd_fail(h, (cpd_status)hs, "layout build failed on the device");
