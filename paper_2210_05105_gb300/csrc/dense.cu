@@ -1247,7 +1247,7 @@ cpd_status cpd_solve_renorm(cpd_ctx* h, int mode, const float* Y, double* out_si
     size_t shm = (size_t)(R * rb) * sizeof(float);
     int nblk = h->gram_blocks;                  // column partials summed by sigma_kernel
     if (rb == 32) {
-      // two resident blocks per SM (118 registers a thread)
+      // two resident blocks per SM (its launch bounds cap it at 128 registers a thread)
       nblk = (int)std::min<int64_t>(std::min(nblk, h->num_sms * 2), std::max<int64_t>(cpd_ceil_div(I, SOLVE_TR), 1));
       solve_lane_kernel<<<nblk, DTHREADS, 0, h->stream>>>(Y, h->Gnpinv_split, h->Uwork, I, R, h->Rp, h->colsq);
     } else if (rb == 16)
