@@ -19,7 +19,8 @@ STATUS = {0: "CPD_OK", 1: "CPD_ERR_INVALID_ARG", 2: "CPD_ERR_OUT_OF_RANGE_INDEX"
           8: "CPD_ERR_TIMEOUT", 9: "CPD_ERR_NOT_FINITE"}
 EXPORTS = ["cpd_default_options", "cpd_create", "cpd_leverage_sample", "cpd_sampled_mttkrp", "cpd_exact_mttkrp",
            "cpd_gram_solve", "cpd_als_sweep", "cpd_fit", "cpd_get_factors", "cpd_set_factors", "cpd_get_sigma",
-           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count", "cpd_sampled_mttkrp_noalloc", "cpd_sts_rescans", "cpd_debug_gram_wait", "cpd_synchronize",
+           "cpd_get_arls_state", "cpd_get_gram", "cpd_profile", "cpd_profile_read", "cpd_sweep_kernel_count",
+           "cpd_sampled_mttkrp_noalloc", "cpd_sts_rescans", "cpd_debug_gram_wait", "cpd_synchronize",
            "cpd_batch_create", "cpd_batch_sweep", "cpd_batch_synchronize", "cpd_batch_destroy", "cpd_autotune",
            "cpd_last_error", "cpd_destroy"]
 PHASES = ["pinv", "draw", "probe", "scan", "spmm", "solve", "gram", "sampler", "exact", "clear"]
